@@ -1,0 +1,180 @@
+"""Seeded synthetic workloads: parameter sets and initial fields.
+
+This module only places droplets/bubbles and draws random numbers. It holds none of the
+method's arithmetic (no lattice, stencil, collision or near-contact code) so that the CUDA path
+and the CPU reference can both take their inputs from it.
+
+Initial fields follow the usual diffuse-interface set-up: every droplet (or bubble) is a
+hyperbolic-tangent profile of width ``eps`` around its radius, phi = 1 in the liquid, and each
+droplet carries its own uniform velocity weighted by its own profile.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+#: Near-contact detection and force parameters printed in Sec. 2.3.2 (w, q_th, eta, cos_opp) and
+#: Sec. 2.2.6 / Eq. 71 (h0 = 1 lattice unit, p = 4); eps_q and eps_n are small floors.
+PAPER_NCI = dict(nci_on=1, w=3, q_th=0.125, eta=0.1, cos_opp=-0.8, h0=1.0, p=4.0,
+                 eps_q=1e-12, eps_n=1e-12)
+
+Q30 = float(1 << 30)
+
+
+def base_config(dim, nx, ny, nz, Q, **kw):
+    cfg = dict(dim=dim, nx=nx, ny=ny, nz=nz, Q=Q, rho_l=1.0, rho_g=1.0, nu_l=0.005, nu_g=0.05,
+               sigma=0.02, eps=4.0, D=0.1, A_rep=0.02, g=(0.0, 0.0, 0.0))
+    cfg.update(PAPER_NCI)
+    cfg.update(kw)
+    return cfg
+
+
+def ncells(cfg):
+    return cfg["nx"] * cfg["ny"] * cfg["nz"]
+
+
+def to_q30_grid(phi):
+    """Round phi to the nearest multiple of 2^-30 so that a fixed-point store holds it exactly."""
+    return np.round(np.asarray(phi, dtype=np.float64) * Q30) / Q30
+
+
+def _coords(cfg):
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    return x.ravel().astype(np.float64), y.ravel().astype(np.float64), z.ravel().astype(np.float64)
+
+
+def _min_image(d, L):
+    return d - L * np.round(d / L)
+
+
+def droplet_fields(cfg, centers, radii, velocities, bubbles=False):
+    """phi and u (shape (3, N)) for a set of droplets (liquid inside) or bubbles (gas inside).
+
+    Droplets: phi = min(1, sum_k prof_k); bubbles: phi = max(0, 1 - sum_k prof_k), with
+    prof_k = (1 + tanh(2 (R_k - r_k) / eps)) / 2 and r_k the minimum-image distance to centre k.
+    u = sum_k prof_k U_k.
+    """
+    eps = cfg["eps"]
+    x, y, z = _coords(cfg)
+    N = x.size
+    prof_sum = np.zeros(N)
+    u = np.zeros((3, N))
+    for c, R, U in zip(centers, radii, velocities):
+        dx = _min_image(x - c[0], cfg["nx"])
+        dy = _min_image(y - c[1], cfg["ny"])
+        dz = _min_image(z - c[2], cfg["nz"]) if cfg["dim"] == 3 else 0.0 * z
+        r = np.sqrt(dx * dx + dy * dy + dz * dz)
+        prof = 0.5 * (1.0 + np.tanh(2.0 * (R - r) / eps))
+        prof_sum += prof
+        for a in range(3):
+            u[a] += prof * U[a]
+    phi = np.maximum(0.0, 1.0 - prof_sum) if bubbles else np.minimum(1.0, prof_sum)
+    return phi, u
+
+
+# --------------------------------------------------------------------------------------------
+# The five workloads (sizes, lattices, physical parameters) and their initial fields.
+# --------------------------------------------------------------------------------------------
+
+def c1_head_on_2d():
+    """2D head-on collision, 128x64 D2Q9, R = 16, centres 40 apart, +-0.02, density ratio 1."""
+    cfg = base_config(2, 128, 64, 1, 9, steps=200)
+    phi, u = droplet_fields(cfg, [(43.5, 31.5, 0.0), (83.5, 31.5, 0.0)], [16.0, 16.0],
+                            [(0.02, 0, 0), (-0.02, 0, 0)])
+    return cfg, phi, u
+
+
+def c2_offcentre_3d(seed=17481, nx=128, ny=64, nz=64, R=12.0):
+    """3D collision, 128x64x64 D3Q19, R = 12, separation 2R + 8 along x, impact offset
+    b ~ U(0, 1) * R along y, relative speed 0.04, density ratio 10."""
+    cfg = base_config(3, nx, ny, nz, 19, rho_g=0.1, steps=2000)
+    rng = np.random.default_rng(seed)
+    b = float(rng.uniform(0.0, 1.0)) * R
+    cx, cy, cz = (nx - 1) / 2.0, (ny - 1) / 2.0, (nz - 1) / 2.0
+    sep = 2 * R + 8
+    centers = [(cx - sep / 2, cy - b / 2, cz), (cx + sep / 2, cy + b / 2, cz)]
+    phi, u = droplet_fields(cfg, centers, [R, R], [(0.02, 0, 0), (-0.02, 0, 0)])
+    cfg["impact_offset"] = b
+    return cfg, phi, u
+
+
+def c3_head_on_3d(nx=256, ny=128, nz=128, R=24.0, Q=19):
+    """3D head-on collision, 256x128x128 D3Q19, R = 24, separation 2R + 8, speed 0.04, ratio 100."""
+    cfg = base_config(3, nx, ny, nz, Q, rho_g=0.01, steps=5000)
+    cx, cy, cz = (nx - 1) / 2.0, (ny - 1) / 2.0, (nz - 1) / 2.0
+    sep = 2 * R + 8
+    centers = [(cx - sep / 2, cy, cz), (cx + sep / 2, cy, cz)]
+    phi, u = droplet_fields(cfg, centers, [R, R], [(0.02, 0, 0), (-0.02, 0, 0)])
+    return cfg, phi, u
+
+
+def swarm_centres(L, nb, rmin, rmax, eps, seed=17481, max_tries=2_000_000):
+    """Rejection-sampled non-overlapping bubbles in a periodic cube: centre distance >= R_i + R_j + eps."""
+    rng = np.random.default_rng(seed)
+    cs, rs = [], []
+    tries = 0
+    while len(cs) < nb and tries < max_tries:
+        tries += 1
+        c = rng.uniform(0.0, L, size=3)
+        r = rng.uniform(rmin, rmax)
+        ok = True
+        for c2, r2 in zip(cs, rs):
+            d = _min_image(c - c2, L)
+            if math.sqrt(float(d @ d)) < r + r2 + eps:
+                ok = False
+                break
+        if ok:
+            cs.append(c)
+            rs.append(r)
+    return np.array(cs), np.array(rs)
+
+
+def c5_swarm(L=512, nb=1500, seed=17481, rmin=8.0, rmax=12.0):
+    """Buoyant bubble swarm, L^3 D3Q19, nb bubbles R ~ U[8, 12], ratio 100, g = 1e-6, sigma = 0.01."""
+    cfg = base_config(3, L, L, L, 19, rho_g=0.01, sigma=0.01, nu_l=1e-3, nu_g=1e-2, A_rep=0.01,
+                      g=(0.0, 0.0, -1e-6), steps=10000)
+    cs, rs = swarm_centres(L, nb, rmin, rmax, cfg["eps"], seed=seed)
+    cfg["n_bubbles"] = len(cs)
+    return cfg, cs, rs
+
+
+def smooth_random_fields(cfg, seed, n_modes=4, amp_u=0.03, pairs=True):
+    """Random smooth periodic phi in (0, 1) with sharp-ish interfaces plus a smooth random u.
+
+    phi = (1 + tanh(s)) / 2 of a sum of random low Fourier modes; with ``pairs`` the box also
+    holds two droplets close enough for their interfaces to face each other.
+    """
+    rng = np.random.default_rng(seed)
+    x, y, z = _coords(cfg)
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    s = np.zeros(x.size)
+    for _ in range(n_modes):
+        kx, ky = rng.integers(-2, 3, size=2)
+        kz = rng.integers(-2, 3) if cfg["dim"] == 3 else 0
+        ph = rng.uniform(0, 2 * np.pi)
+        s += rng.normal() * np.cos(2 * np.pi * (kx * x / nx + ky * y / ny + kz * z / nz) + ph)
+    phi = 0.5 * (1.0 + np.tanh(1.5 * s))
+    if pairs:
+        R = max(2.0, min(nx, ny) / 5.0)
+        cz = (nz - 1) / 2.0
+        centers = [(nx / 2.0 - R - 1.3, ny / 2.0 + 0.3, cz), (nx / 2.0 + R + 1.1, ny / 2.0 - 0.4, cz)]
+        pd, _ = droplet_fields(cfg, centers, [R, R], [(0, 0, 0), (0, 0, 0)])
+        m = pd > 0.02
+        phi = np.where(m, pd, phi)
+    u = np.zeros((3, x.size))
+    dims = 3 if cfg["dim"] == 3 else 2
+    for a in range(dims):
+        for _ in range(2):
+            kx, ky = rng.integers(-2, 3, size=2)
+            kz = rng.integers(-2, 3) if cfg["dim"] == 3 else 0
+            ph = rng.uniform(0, 2 * np.pi)
+            u[a] += amp_u / 2 * rng.normal() * np.cos(
+                2 * np.pi * (kx * x / nx + ky * y / ny + kz * z / nz) + ph)
+    return phi, u
+
+
+def noise(shape, seed, scale=1.0):
+    """Seeded standard-normal noise (used to push populations off equilibrium in tests)."""
+    return scale * np.random.default_rng(seed).standard_normal(shape)
