@@ -1,0 +1,400 @@
+"""Throughput benchmark of the per-step lattice update (near-contact interaction + regularized
+LB hydrodynamics + conservative Allen-Cahn phase field) on one GB300 per rank.
+
+Workload: the 3D head-on collision at 256x128x128 (D3Q19, R = 24, density ratio 100), seeded
+synthetic fields. One step = one near-contact pass, one hydrodynamic pass and one phase-field
+pass over all cells. The populations (2 x 319 MB in FP32) exceed the 129 MB L2, so no flush is
+needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--store f32|f16|bf16]
+
+Prints one JSON line (rank 0). Multi-GPU (torchrun): every rank runs its own independent copy of
+the workload (weak scaling, no data-path collective); the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & HBM-roofline fraction, FP32 vs FP16-store at stated φ error vs FP64"
+WORKLOAD = "3D head-on droplet collision 256x128x128 D3Q19, R=24, W=4, density ratio 100"
+HBM_FALLBACK_GBS = 6800.0
+# Algorithmic bytes per cell update (stored state only): populations read + written, phi read +
+# written, velocity written + read.
+def step_bytes_per_cell(Q, pop_bytes):
+    return 2 * Q * pop_bytes + 8 + 24
+
+
+def hydro_bytes_per_cell(Q, pop_bytes):
+    # hydrodynamic kernel: populations read + written, phi read, velocity written
+    return 2 * Q * pop_bytes + 4 + 12
+
+
+# DRAM traffic of one hydrodynamic launch on the full workload, from the ncu capture summarised in
+# profiles/ (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hydro kernel source hash:
+# a changed kernel reports null until it is profiled again.
+HYDRO_TRAFFIC = {}
+
+
+def _src_hash(*names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2603_17481_gb300", "csrc", n), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value, device=None):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_workload():
+    from paper_2603_17481_gb300 import workloads as W
+    cfg, phi, u = W.c3_head_on_3d()
+    phi = W.to_q30_grid(phi)
+    return cfg, phi, u
+
+
+def cpu_oracle_run(cfg, phi, u, budget_s, max_steps=5, min_steps=1):
+    """Times the FP64 oracle (as it stands) on the full grid for a bounded number of steps."""
+    import oracle
+    P = oracle.make_params(cfg)
+    f = oracle.init(P, phi, u)
+    N = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    steps, t_total = 0, 0.0
+    ph = phi
+    while steps < max_steps and (steps < min_steps or t_total < budget_s):
+        t0 = time.perf_counter()
+        f, ph, _ = oracle.step(P, f, ph, 1)
+        t_total += time.perf_counter() - t0
+        steps += 1
+    return N * steps / t_total / 1e6, steps, t_total
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2603_17481_gb300 import binding as B
+    from paper_2603_17481_gb300 import build as lbm_build
+
+    torch.cuda.set_device(local)
+    lbm_build.build()
+    cfg, phi, u = make_workload()
+    N = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    Q = cfg["Q"]
+    stream = torch.cuda.Stream()
+    sim = B.Lbm(cfg, store=args.store, stream=stream.cuda_stream)
+    sim.init_fields(phi, u)
+    m0, _ = sim.mass()
+
+    # warm-up
+    sim.step(args.warmup)
+    sim.synchronize()
+
+    # timed region: K steps, per-kernel events on the library stream
+    sampler = ClockSampler(local)
+    sim.profile(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        sim.step(1)
+    ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    prof = sim.profile_read()
+    sim.profile(False)
+    ms_total = ev0.elapsed_time(ev1)
+    ms_max = max_over_ranks(world, ms_total, device=f"cuda:{local}")
+    m1, _ = sim.mass()
+
+    pop_b = 4 if args.store == "f32" else 2
+    mlups = world * N * args.steps / (ms_max * 1e-3) / 1e6
+    peak, peak_kind = measured_peaks()
+    hydro_ms, hydro_n = prof["hydro"]
+    hydro_avg = hydro_ms / max(hydro_n, 1)
+    per_launch_bytes = hydro_bytes_per_cell(Q, pop_b) * N
+    achieved = per_launch_bytes / (hydro_avg * 1e-3) / 1e9
+    key = (args.store, _src_hash("hydro_impl.cuh", "lbm_device.cuh"))
+    traffic = HYDRO_TRAFFIC.get(key)
+    gpu_launches = int(sum(n for k, (ms, n) in prof.items()))
+
+    step_frac = mlups / world * 1e6 * step_bytes_per_cell(Q, pop_b) / (peak * 1e9)
+
+    # end-to-end through the C ABI with pinned host buffers: H2D of the initial fields, one
+    # lbm_step call per step, D2H of the final fields
+    e2e = None
+    if not args.no_e2e:
+        phi_h = torch.from_numpy(np.ascontiguousarray(phi)).pin_memory()
+        u_h = torch.from_numpy(np.ascontiguousarray(u)).reshape(-1).pin_memory()
+        out_phi = torch.empty(N, dtype=torch.float64).pin_memory()
+        out_u = torch.empty(3 * N, dtype=torch.float64).pin_memory()
+        out_ps = torch.empty(N, dtype=torch.float64).pin_memory()
+        ke = args.steps
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.init_fields(phi_h, u_h)
+        for _ in range(ke):
+            sim.step(1)
+        sim.read_fields(phi=out_phi, u=out_u, pstar=out_ps)
+        t1 = time.perf_counter()
+        dt = max_over_ranks(world, t1 - t0, device=f"cuda:{local}")
+        h2d = (phi_h.numel() + u_h.numel()) * 8
+        d2h = (out_phi.numel() + out_u.numel() + out_ps.numel()) * 8
+        e2e = {"value": round(world * N * ke / dt / 1e6, 1), "unit": "MLUPS",
+               "h2d_bytes_per_step": round(h2d / ke, 1), "d2h_bytes_per_step": round(d2h / ke, 1),
+               "steps": ke, "what": "lbm_init_fields(pinned host) + steps x lbm_step(1) + lbm_read_fields(pinned host)"}
+
+    variants = {}
+    if args.variants and args.store == "f32" and world == 1:
+        ph32, _, _ = sim.read_fields(want=("phi",))
+        for st in ("f16", "bf16"):
+            s2 = B.Lbm(cfg, store=st, stream=stream.cuda_stream)
+            s2.init_fields(phi, u)
+            s2.step(args.warmup)
+            s2.synchronize()
+            kv = max(args.steps // 2, 10)
+            s2.profile(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(kv):
+                s2.step(1)
+            e1.record(stream)
+            e1.synchronize()
+            pr = s2.profile_read()
+            msv = e0.elapsed_time(e1)
+            hm, hn = pr["hydro"]
+            v_mlups = N * kv / (msv * 1e-3) / 1e6
+            # phi after the same number of steps as the FP32 run, compared with it
+            s2.init_fields(phi, u)
+            s2.step(args.warmup + args.steps)
+            ph2, _, _ = s2.read_fields(want=("phi",))
+            variants[st] = {
+                "value": round(v_mlups, 1), "steps": kv,
+                "hydro_gbs": round(hydro_bytes_per_cell(Q, 2) * N / (hm / hn * 1e-3) / 1e9, 1),
+                "step_roofline_frac": round(v_mlups * 1e6 * step_bytes_per_cell(Q, 2) / (peak * 1e9), 4),
+                "max_abs_phi_diff_vs_f32_after_%d_steps" % (args.warmup + args.steps):
+                    float(np.max(np.abs(ph2 - ph32))),
+            }
+            s2.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, steps, tt = cpu_oracle_run(cfg, phi, u, budget_s=args.cpu_budget)
+        cpu = {"value": round(v, 4), "unit": "MLUPS", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{steps} FP64 oracle step(s) of the full 256x128x128 grid, {tt:.1f} s, "
+                         f"OpenMP over all host cores"}
+
+    sim.close()
+    if rank != 0:
+        return None
+    line = {
+        "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.store == "f32" else f"f32 ({args.store} store)",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": N, "lattice": "D3Q19 hydro, D3Q27 phase-field stencils",
+                   "store": args.store, "near_contact": "on (w=3, q_th=0.125, eta=0.1, cos=-0.8)",
+                   "l2": "inputs larger than L2 (2 x %.0f MB populations), no flush" % (Q * N * pop_b / 1e6),
+                   "parallelism": f"{world} independent replica(s), one per GPU"},
+        "roofline": {"bound": "hbm", "kernel": "hydro", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "bytes_per_cell": hydro_bytes_per_cell(Q, pop_b), "avg_ms": round(hydro_avg, 5),
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"},
+        "step_roofline": {"bytes_per_cell": step_bytes_per_cell(Q, pop_b), "frac_of_measured": round(step_frac, 4),
+                          "frac_of_8TBs": round(step_frac * peak / 8000.0, 4)},
+        "kernels_ms_per_step": {k: round(ms / max(n, 1), 5) for k, (ms, n) in prof.items() if n},
+        "gpu_launches": gpu_launches,
+        "clocks": clocks,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "phi_mass_drift": abs(m1 - m0) / abs(m0),
+    }
+    if variants:
+        line["variants"] = variants
+    return line
+
+
+def run_reference(args, world, rank):
+    """The FP64 CPU oracle as the reference arm, each step a bounded crop of the same workload."""
+    if rank != 0:
+        return None
+    import numpy as np
+
+    import oracle
+    from paper_2603_17481_gb300 import workloads as W
+    oracle.build()
+    cfg, phi, u = make_workload()
+    # calibrate: oracle throughput on a 64x32x32 crop of the workload
+    budget = args.ref_budget / max(args.steps + args.warmup, 1)
+
+    def crop(nx, ny, nz):
+        g = phi.reshape(cfg["nz"], cfg["ny"], cfg["nx"])
+        x0, y0, z0 = (cfg["nx"] - nx) // 2 - 28, (cfg["ny"] - ny) // 2, (cfg["nz"] - nz) // 2
+        x0 = max(x0, 0)
+        p = g[z0:z0 + nz, y0:y0 + ny, x0:x0 + nx].ravel().copy()
+        uu = u.reshape(3, cfg["nz"], cfg["ny"], cfg["nx"])[:, z0:z0 + nz, y0:y0 + ny, x0:x0 + nx].reshape(3, -1).copy()
+        c = dict(cfg, nx=nx, ny=ny, nz=nz)
+        return c, p, uu
+
+    c, p, uu = crop(64, 32, 32)
+    P = oracle.make_params(c)
+    f = oracle.init(P, p, uu)
+    t0 = time.perf_counter()
+    oracle.step(P, f, p, 1)
+    rate = 64 * 32 * 32 / (time.perf_counter() - t0)
+    side = max(8, int(round((rate * budget / 2) ** (1 / 3))))
+    nx, ny, nz = min(2 * side, cfg["nx"]), min(side, cfg["ny"]), min(side, cfg["nz"])
+    c, p, uu = crop(nx, ny, nz)
+    P = oracle.make_params(c)
+    f = oracle.init(P, p, uu)
+    ph = p
+    for _ in range(args.warmup):
+        f, ph, _ = oracle.step(P, f, ph, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f, ph, _ = oracle.step(P, f, ph, 1)
+    dt = time.perf_counter() - t0
+    N = nx * ny * nz
+    v = N * args.steps / dt / 1e6
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"{nx}x{ny}x{nz} central crop per step"},
+        "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "value": round(v, 4), "unit": "MLUPS",
+                         "sample": f"each step: one FP64 oracle step on a {nx}x{ny}x{nz} crop of the workload"},
+        "e2e": {"value": round(v, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--store", choices=["f32", "f16", "bf16"], default="f32")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", dest="variants", action="store_false")
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
+    ap.add_argument("--ref-budget", type=float, default=120.0, help="seconds for the whole reference arm")
+    args = ap.parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        line = run_reference(args, world, rank)
+    else:
+        line = run_ours(args, world, rank, local)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

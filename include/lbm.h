@@ -1,0 +1,146 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) library for one time step of the conservative Allen-Cahn
+ * phase-field lattice Boltzmann model with adaptive near-contact repulsion of arXiv 2603.17481.
+ *
+ * One step advances, on a fully periodic box,
+ *   (1) the near-contact interaction: interfacial gate, bounded-window partner search and the
+ *       closed-form proximity indicator / repulsive force (Sec. 2.3, Eqs. 57-73);
+ *   (2) the thread-safe recursive-regularized lattice Boltzmann hydrodynamics with Guo forcing and
+ *       the force split F = F_sigma + F_p + F_nu + F_rep + F_ext (Sec. 2.1, Eqs. 3-23), as a pull
+ *       scheme over structure-of-arrays populations;
+ *   (3) the conservative Allen-Cahn phase field phi^{n+1} = phi^n - div(u phi) + D lap(phi) + S_comp
+ *       with MUSCL-minmod advection and isotropic stencils (Sec. 2.1.1, Eqs. 24-35),
+ * in that order: the hydrodynamics at step n uses phi^n and produces u^n, which advects phi^n.
+ *
+ * Conventions shared by every call:
+ *   - cell index n = x + nx*(y + ny*z), x fastest; nz = 1 when dim = 2.
+ *   - host arrays are FP64, owned by the caller, read or written only during the call.
+ *   - vector fields are structure-of-arrays with 3 rows: v[a*N + n], a = 0..2 (the z row is
+ *     ignored on input and written as 0 on output when dim = 2).
+ *   - populations f[i*N + n] are the PRE-collision populations of the current step at cell n.
+ *   - velocity order i = 0..Q-1: sorted by |c|^2 ascending, ties by (c_z, c_y, c_x) in
+ *     lexicographic order with -1 < 0 < +1 (lbm_lattice() returns the table).
+ *   - phi = 1 in the liquid, 0 in the gas; density rho(phi) = rho_g + (rho_l - rho_g) phi; the
+ *     normalised pressure p* gives the pressure p = rho c_s^2 p* (Eq. 5), c_s^2 = 1/3.
+ *   - every entry point returns LBM_OK (0) or a negative lbm_status; none aborts, exits or traps.
+ *     After LBM_ERR_CUDA the context must be destroyed.
+ *   - calls on one context are not thread-safe; different contexts are independent.
+ *   - the library owns all device memory of a context (allocated in lbm_create / on first use).
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = -1,      /* invalid argument or parameter set                                   */
+  LBM_ERR_OOM = -2,      /* device memory allocation failed                                     */
+  LBM_ERR_CUDA = -3,     /* CUDA runtime error (no device, launch or copy failure)              */
+  LBM_ERR_UNSTABLE = -4, /* periodic check found NaN/Inf or a phi-mass drift above mass_tol     */
+  LBM_ERR_STATE = -5     /* call out of order (e.g. lbm_step before lbm_init_fields)            */
+} lbm_status;
+
+typedef enum {
+  LBM_STORE_F32 = 0,  /* populations stored as FP32                                             */
+  LBM_STORE_F16 = 1,  /* populations stored as FP16, f_i / w_i (deviation from rest, p* = 0)    */
+  LBM_STORE_BF16 = 2  /* populations stored as BF16, f_i / w_i                                  */
+} lbm_store;
+
+/* Kernel kinds reported by the profiler (lbm_profile_read). */
+typedef enum {
+  LBM_K_NCI = 0, LBM_K_HYDRO = 1, LBM_K_PHASE = 2, LBM_K_REDUCE = 3, LBM_K_CONVERT = 4,
+  LBM_K_COUNT = 5
+} lbm_kernel_kind;
+
+typedef struct {
+  int dim;            /* 2 or 3                                                                 */
+  int nx, ny, nz;     /* periodic box; nz = 1 when dim = 2                                     */
+  int Q;              /* hydrodynamic lattice: 9 (dim 2), 19 or 27 (dim 3)                      */
+  int store;          /* lbm_store                                                              */
+  double rho_l, rho_g;/* liquid / gas densities (> 0)                                           */
+  double nu_l, nu_g;  /* kinematic viscosities (> 0); dynamic viscosity mixes linearly (Eq. 8)  */
+  double sigma;       /* surface tension; chemical potential 4 beta phi(phi-1)(phi-1/2) - k lap */
+                      /* phi with beta = 12 sigma / eps, k = 3 sigma eps / 2 (Eq. 19)           */
+  double eps;         /* interface width epsilon (> 0): tanh profile width, kappa = 4 D / eps  */
+                      /* (Eq. 26), proximity indicator scale (Eq. 70)                            */
+  double D;           /* phase-field diffusivity (>= 0), tau_diff of Eq. 28                     */
+  int nci_on;         /* near-contact interaction on (1) / off (0)                              */
+  int w;              /* search-window radius, 1..3 (Eq. 60; paper: 3)                          */
+  double A_rep;       /* repulsion amplitude (Eq. 72; paper: O(sigma))                          */
+  double h0, p;       /* thickness weight 1/(1+(h/h0)^p) (Eq. 42; paper: h0 = 1, p = 4)        */
+  double q_th;        /* interfacial gate (Eq. 59; paper 0.125)                                 */
+  double eta;         /* iso-interface tolerance (Eq. 61; paper 0.1)                            */
+  double cos_opp;     /* facing threshold (Eq. 62; paper -0.8)                                  */
+  double eps_q, eps_n;/* floors of Eqs. 67 and 57                                               */
+  double g[3];        /* body acceleration; F_ext = (rho - rho_bar) g, rho_bar = mean initial rho */
+  int mass_check_every; /* lbm_step runs the FP64 phi-mass / NaN check every this many steps; 0 = off */
+  double mass_tol;    /* relative phi-mass drift that makes the check fail                      */
+} lbm_params;
+
+/* Fills *p with the paper's near-contact parameters (Sec. 2.3.2, Eq. 71) on a 64^3 D3Q19 box. */
+void lbm_params_default(lbm_params *p);
+
+/* Validates *p (LBM_ERR_ARG before any CUDA call), then allocates the device state of a context
+ * on the current CUDA device. *out is set only on success. */
+int lbm_create(const lbm_params *p, lbm_ctx **out);
+
+/* Frees every device buffer of ctx; ctx may be NULL. */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Kernels and copies of ctx go to this cudaStream_t (NULL = the legacy default stream). Calls
+ * still return only after their work is complete, except lbm_step (see below). */
+int lbm_set_stream(lbm_ctx *ctx, void *stream);
+
+/* Initial state: phi (N), u (3N) and p* (N, or NULL for p* = 0) on the host. Populations become
+ * the third-order equilibrium f_eq(p*, u) (Eq. 11); rho_bar is the mean of rho(phi). */
+int lbm_init_fields(lbm_ctx *ctx, const double *phi, const double *u, const double *pstar);
+
+/* Full state: pre-collision populations f (Q*N) and phi (N). rho_bar becomes the mean rho(phi). */
+int lbm_set_state(lbm_ctx *ctx, const double *f, const double *phi);
+/* Reads the full state back (f: Q*N, phi: N; either may be NULL). */
+int lbm_get_state(lbm_ctx *ctx, double *f, double *phi);
+
+/* Advances n >= 0 steps. Enqueues the work on the context stream and returns; it synchronises
+ * only when the periodic mass check runs (mass_check_every > 0), which may return
+ * LBM_ERR_UNSTABLE. */
+int lbm_step(lbm_ctx *ctx, int n);
+
+/* phi^n (N), the velocity u (3N) and p* (N) of the current state: moments of the pre-collision
+ * populations with the forces evaluated on phi^n (Eqs. 6-7, with F_nu from u without F_nu).
+ * Any output pointer may be NULL. */
+int lbm_read_fields(lbm_ctx *ctx, double *phi, double *u, double *pstar);
+
+/* FP64 integrals of the current state: sum(phi) (exact sum of the stored fixed-point phi) and
+ * sum(rho u) (3 values, u as in lbm_read_fields). Either pointer may be NULL. */
+int lbm_mass(lbm_ctx *ctx, double *phi_mass, double *mom);
+
+/* Near-contact diagnostics on the current phi: partner offsets (3 int32 per cell, INT32_MIN where
+ * chi = 0) and the repulsive force density F_rep (3N). Either pointer may be NULL. */
+int lbm_read_nci(lbm_ctx *ctx, int32_t *partner, double *frep);
+
+/* Waits for all work of ctx. */
+int lbm_synchronize(lbm_ctx *ctx);
+
+/* Per-kernel timing with CUDA events on the context stream (enable = 1 starts a fresh tally). */
+int lbm_profile(lbm_ctx *ctx, int enable);
+/* Accumulated device milliseconds and launch counts per lbm_kernel_kind (arrays of LBM_K_COUNT;
+ * either may be NULL). Synchronises the stream. */
+int lbm_profile_read(lbm_ctx *ctx, double *ms, int64_t *launches);
+
+/* Velocity table of a hydrodynamic lattice in the order above: c is 3*Q ints, w is Q doubles. */
+int lbm_lattice(int dim, int Q, int *c, double *w);
+
+const char *lbm_strerror(int status);
+const char *lbm_kernel_name(int kind);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

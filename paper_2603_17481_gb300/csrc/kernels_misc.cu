@@ -1,0 +1,241 @@
+// kernels_misc.cu -- conversions between the FP64 host layout and the device state, equilibrium
+// initialisation, and the FP64 / exact-integer reductions of the periodic conservation check.
+#include "launch.h"
+
+namespace lbm {
+
+cudaError_t launch_hydro_q9(int, int, const KParams &, const void *, void *, const int32_t *, const float4 *,
+                            float *, float *, cudaStream_t);
+cudaError_t launch_hydro_q19(int, int, const KParams &, const void *, void *, const int32_t *, const float4 *,
+                             float *, float *, cudaStream_t);
+cudaError_t launch_hydro_q27(int, int, const KParams &, const void *, void *, const int32_t *, const float4 *,
+                             float *, float *, cudaStream_t);
+
+cudaError_t launch_hydro(int Q, int store, int mode, const KParams &P, const void *src, void *dst,
+                         const int32_t *phi, const float4 *frep, float *u, float *pstar, cudaStream_t s) {
+  switch (Q) {
+    case 9: return launch_hydro_q9(store, mode, P, src, dst, phi, frep, u, pstar, s);
+    case 19: return launch_hydro_q19(store, mode, P, src, dst, phi, frep, u, pstar, s);
+    default: return launch_hydro_q27(store, mode, P, src, dst, phi, frep, u, pstar, s);
+  }
+}
+
+static inline dim3 grid1d(long long n, int bs) {
+  long long g = (n + bs - 1) / bs;
+  return dim3((unsigned)(g < 1 ? 1 : g));
+}
+
+// phi (FP64) -> signed 2.30 fixed point, round to nearest, saturating
+__global__ void k_phi_in(long long N, const double *__restrict__ in, int32_t *__restrict__ out) {
+  long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  double v = in[n] * 1073741824.0;
+  v = fmin(fmax(v, -2147483648.0), 2147483647.0);
+  out[n] = (int32_t)__double2ll_rn(v);
+}
+__global__ void k_phi_out(long long N, const int32_t *__restrict__ in, double *__restrict__ out) {
+  long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  out[n] = (double)in[n] * (1.0 / 1073741824.0);
+}
+__global__ void k_f32_out(long long n_, const float *__restrict__ in, double *__restrict__ out) {
+  long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= n_) return;
+  out[n] = (double)in[n];
+}
+
+cudaError_t launch_phi_in(const KParams &P, const double *phi64, int32_t *phi, cudaStream_t s) {
+  k_phi_in<<<grid1d(P.N, 256), 256, 0, s>>>(P.N, phi64, phi);
+  return cudaGetLastError();
+}
+cudaError_t launch_phi_out(const KParams &P, const int32_t *phi, double *phi64, cudaStream_t s) {
+  k_phi_out<<<grid1d(P.N, 256), 256, 0, s>>>(P.N, phi, phi64);
+  return cudaGetLastError();
+}
+cudaError_t launch_f32_out(long long n, const float *src, double *dst, cudaStream_t s) {
+  k_f32_out<<<grid1d(n, 256), 256, 0, s>>>(n, src, dst);
+  return cudaGetLastError();
+}
+
+__device__ __forceinline__ long long cell_shift(const KParams &P, int x, int y, int z, int cx, int cy, int cz,
+                                                int dim) {
+  int X = x + cx, Y = y + cy, Z = z + cz;
+  X = X < 0 ? X + P.nx : (X >= P.nx ? X - P.nx : X);
+  Y = Y < 0 ? Y + P.ny : (Y >= P.ny ? Y - P.ny : Y);
+  if (dim == 3) Z = Z < 0 ? Z + P.nz : (Z >= P.nz ? Z - P.nz : Z);
+  else Z = 0;
+  return (long long)X + (long long)P.nx * (Y + (long long)P.ny * Z);
+}
+
+// Initial populations f_eq(p*, u) (Eq. 11, evaluated in FP64), stored for the pull scheme:
+// buffer cell y holds the population that streams to y + c_i, i.e. f_eq_i at y + c_i.
+template <class L, int S>
+__global__ void k_init_pops(const KParams P, const double *__restrict__ u64, const double *__restrict__ ps64,
+                            typename Store<S>::T *__restrict__ pops) {
+  long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= P.N) return;
+  int x = (int)(n % P.nx), y = (int)((n / P.nx) % P.ny), z = (int)(n / ((long long)P.nx * P.ny));
+#pragma unroll
+  for (int i = 0; i < L::Q; i++) {
+    long long m = cell_shift(P, x, y, z, L::c(i, 0), L::c(i, 1), L::c(i, 2), L::D);
+    double u0 = u64[m], u1 = u64[P.N + m], u2 = L::D == 3 ? u64[2 * P.N + m] : 0.0;
+    double ps = ps64 ? ps64[m] : 0.0;
+    double cu = L::c(i, 0) * u0 + L::c(i, 1) * u1 + L::c(i, 2) * u2;
+    double uu = u0 * u0 + u1 * u1 + u2 * u2;
+    double feq = L::wd(i) * (ps + 3.0 * cu + 4.5 * (cu * cu - uu / 3.0) + 4.5 * (cu * cu * cu - uu * cu));
+    Store<S>::st(pops + (long long)i * P.N + n, (float)feq, L::w(i));
+  }
+}
+
+// Host pre-collision populations f[i][x] -> pull storage buf[i][x - c_i] = f[i][x].
+template <class L, int S>
+__global__ void k_set_pops(const KParams P, const double *__restrict__ f64, typename Store<S>::T *__restrict__ pops) {
+  long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= P.N) return;
+  int x = (int)(n % P.nx), y = (int)((n / P.nx) % P.ny), z = (int)(n / ((long long)P.nx * P.ny));
+#pragma unroll
+  for (int i = 0; i < L::Q; i++) {
+    long long m = cell_shift(P, x, y, z, L::c(i, 0), L::c(i, 1), L::c(i, 2), L::D);
+    Store<S>::st(pops + (long long)i * P.N + n, (float)f64[(long long)i * P.N + m], L::w(i));
+  }
+}
+
+template <class L, int S>
+__global__ void k_get_pops(const KParams P, const typename Store<S>::T *__restrict__ pops, double *__restrict__ f64) {
+  long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= P.N) return;
+  int x = (int)(n % P.nx), y = (int)((n / P.nx) % P.ny), z = (int)(n / ((long long)P.nx * P.ny));
+#pragma unroll
+  for (int i = 0; i < L::Q; i++) {
+    long long m = cell_shift(P, x, y, z, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2), L::D);
+    f64[(long long)i * P.N + n] = (double)Store<S>::ld(pops + (long long)i * P.N + m, L::w(i));
+  }
+}
+
+template <class L>
+static cudaError_t pops_dispatch_l(int what, int store, const KParams &P, const double *a, const double *b,
+                                   void *pops, double *out, cudaStream_t s) {
+  dim3 g = grid1d(P.N, 128);
+#define LBM_POPS_CASE(SV)                                                                              \
+  case SV: {                                                                                           \
+    using T = typename Store<SV>::T;                                                                   \
+    if (what == 0) k_init_pops<L, SV><<<g, 128, 0, s>>>(P, a, b, (T *)pops);                           \
+    else if (what == 1) k_set_pops<L, SV><<<g, 128, 0, s>>>(P, a, (T *)pops);                          \
+    else k_get_pops<L, SV><<<g, 128, 0, s>>>(P, (const T *)pops, out);                                 \
+    break;                                                                                             \
+  }
+  switch (store) {
+    LBM_POPS_CASE(0)
+    LBM_POPS_CASE(1)
+    LBM_POPS_CASE(2)
+    default: return cudaErrorInvalidValue;
+  }
+#undef LBM_POPS_CASE
+  return cudaGetLastError();
+}
+
+static cudaError_t pops_dispatch(int Q, int what, int store, const KParams &P, const double *a, const double *b,
+                                 void *pops, double *out, cudaStream_t s) {
+  switch (Q) {
+    case 9: return pops_dispatch_l<D2Q9>(what, store, P, a, b, pops, out, s);
+    case 19: return pops_dispatch_l<D3Q19>(what, store, P, a, b, pops, out, s);
+    default: return pops_dispatch_l<D3Q27>(what, store, P, a, b, pops, out, s);
+  }
+}
+
+cudaError_t launch_init_pops(int Q, int store, const KParams &P, const double *u64, const double *ps64, void *pops,
+                             cudaStream_t s) {
+  return pops_dispatch(Q, 0, store, P, u64, ps64, pops, nullptr, s);
+}
+cudaError_t launch_set_pops(int Q, int store, const KParams &P, const double *f64, void *pops, cudaStream_t s) {
+  return pops_dispatch(Q, 1, store, P, f64, nullptr, pops, nullptr, s);
+}
+cudaError_t launch_get_pops(int Q, int store, const KParams &P, const void *pops, double *f64, cudaStream_t s) {
+  return pops_dispatch(Q, 2, store, P, nullptr, nullptr, const_cast<void *>(pops), f64, s);
+}
+
+__global__ void k_frep_out(long long N, int dim, const float4 *__restrict__ frep, double *__restrict__ out) {
+  long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float4 f = frep[n];
+  out[n] = f.x;
+  out[N + n] = f.y;
+  out[2 * N + n] = dim == 3 ? f.z : 0.0;
+}
+cudaError_t launch_partner_frep_out(const KParams &P, int dim, const float4 *frep, double *frep64, cudaStream_t s) {
+  k_frep_out<<<grid1d(P.N, 256), 256, 0, s>>>(P.N, dim, frep, frep64);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Reductions: fixed grid, fixed per-thread strides and a fixed tree, so the FP64 results are
+// reproducible run to run; the phi sum is an exact 64-bit integer sum of the fixed-point field.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+constexpr int kReduceThreads = 256;
+
+__global__ void __launch_bounds__(kReduceThreads)
+k_reduce_partial(const KParams P, const int32_t *__restrict__ phi, const float *__restrict__ u,
+                 ReduceOut *__restrict__ partials) {
+  long long sphi = 0, nonfin = 0;
+  double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < P.N; n += stride) {
+    const int32_t v = phi[n];
+    sphi += v;
+    const double rho = P.rho_g64 + P.drho64 * ((double)v * (1.0 / 1073741824.0));
+    const float a = u[n], b = u[P.N + n], c = u[2 * P.N + n];
+    if (!isfinite(a) || !isfinite(b) || !isfinite(c)) nonfin++;
+    m0 += rho * a;
+    m1 += rho * b;
+    m2 += rho * c;
+  }
+  __shared__ double sm[3][kReduceThreads / 32];
+  __shared__ long long sl[2][kReduceThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  m0 = warp_sum(m0); m1 = warp_sum(m1); m2 = warp_sum(m2);
+  sphi = warp_sum_ll(sphi); nonfin = warp_sum_ll(nonfin);
+  if (lane == 0) {
+    sm[0][wid] = m0; sm[1][wid] = m1; sm[2][wid] = m2;
+    sl[0][wid] = sphi; sl[1][wid] = nonfin;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ReduceOut r{0, {0.0, 0.0, 0.0}, 0};
+    for (int k = 0; k < kReduceThreads / 32; k++) {
+      r.mom[0] += sm[0][k]; r.mom[1] += sm[1][k]; r.mom[2] += sm[2][k];
+      r.phi_q30 += sl[0][k]; r.nonfinite += sl[1][k];
+    }
+    partials[blockIdx.x] = r;
+  }
+}
+
+__global__ void k_reduce_final(const ReduceOut *__restrict__ partials, int n, ReduceOut *__restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  ReduceOut r{0, {0.0, 0.0, 0.0}, 0};
+  for (int k = 0; k < n; k++) {
+    r.phi_q30 += partials[k].phi_q30;
+    r.nonfinite += partials[k].nonfinite;
+    for (int a = 0; a < 3; a++) r.mom[a] += partials[k].mom[a];
+  }
+  *out = r;
+}
+
+cudaError_t launch_reduce(const KParams &P, const int32_t *phi, const float *u, ReduceOut *partials, ReduceOut *out,
+                          cudaStream_t s) {
+  k_reduce_partial<<<kReduceBlocks, kReduceThreads, 0, s>>>(P, phi, u, partials);
+  k_reduce_final<<<1, 32, 0, s>>>(partials, kReduceBlocks, out);
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

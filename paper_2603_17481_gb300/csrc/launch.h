@@ -1,0 +1,49 @@
+// launch.h -- host-side launchers of the liblbm kernels (internal to the library).
+#pragma once
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// Window offsets of the near-contact search, sorted by (|r|^2, canonical index), passed by value.
+struct NciTable {
+  NciOffset o[kMaxOffsets];
+  int count;
+};
+
+// Kernel modes of the hydrodynamic kernel.
+enum HydroMode { kStep = 0, kMoments = 1 };
+
+cudaError_t launch_nci(int dim, const KParams &P, const NciTable &T, const int32_t *phi, float4 *frep,
+                       int32_t *partner, int debug, cudaStream_t s);
+
+// src/dst are population buffers of the store type; MODE kStep writes dst and u, kMoments writes
+// u and pstar only.
+cudaError_t launch_hydro(int Q, int store, int mode, const KParams &P, const void *src, void *dst,
+                         const int32_t *phi, const float4 *frep, float *u, float *pstar, cudaStream_t s);
+
+cudaError_t launch_phase(int dim, const KParams &P, const int32_t *phi, const float *u, int32_t *phi_out,
+                         cudaStream_t s);
+
+// Conversions between host-layout FP64 staging buffers and the device state.
+cudaError_t launch_phi_in(const KParams &P, const double *phi64, int32_t *phi, cudaStream_t s);
+cudaError_t launch_phi_out(const KParams &P, const int32_t *phi, double *phi64, cudaStream_t s);
+cudaError_t launch_f32_out(long long n, const float *src, double *dst, cudaStream_t s);
+cudaError_t launch_init_pops(int Q, int store, const KParams &P, const double *u64, const double *ps64,
+                             void *pops, cudaStream_t s);
+cudaError_t launch_set_pops(int Q, int store, const KParams &P, const double *f64, void *pops, cudaStream_t s);
+cudaError_t launch_get_pops(int Q, int store, const KParams &P, const void *pops, double *f64, cudaStream_t s);
+cudaError_t launch_partner_frep_out(const KParams &P, int dim, const float4 *frep, double *frep64,
+                                    cudaStream_t s);
+
+// FP64 / exact-integer reductions over the current fields.
+struct ReduceOut {
+  long long phi_q30;  // exact sum of the fixed-point phi
+  double mom[3];      // sum of rho(phi) u
+  long long nonfinite;
+};
+constexpr int kReduceBlocks = 608;  // 4 per SM of a 152-SM GB300
+cudaError_t launch_reduce(const KParams &P, const int32_t *phi, const float *u, ReduceOut *partials,
+                          ReduceOut *out, cudaStream_t s);
+
+}  // namespace lbm

@@ -1,0 +1,542 @@
+// lbm_api.cu -- the C ABI of include/lbm.h: context lifetime, device memory, host <-> device
+// conversions, the per-step launch sequence, the periodic conservation check and the profiler.
+//
+// Device memory of a context (N cells, Q directions, store type T):
+//   pop[2]   Q*N T        ping-pong population buffers (pull scheme, structure of arrays)
+//   phi[2]   N int32      fixed-point phi, ping-pong
+//   u        3*N float    velocity of the last hydrodynamic pass (advects phi)
+//   frep     N float4     near-contact force, valid at gated cells only
+//   mom      4*N float    u and p* of lbm_read_fields / lbm_mass (allocated on first use)
+//   stage    k*N double   FP64 staging of host I/O (allocated on first use, grown as needed)
+//   red      reduction partials and result
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "launch.h"
+
+using namespace lbm;
+
+struct ProfPair {
+  int kind;
+  cudaEvent_t a, b;
+};
+
+struct lbm_ctx {
+  lbm_params P;
+  KParams K;
+  NciTable T;
+  long long N;
+  size_t pop_bytes;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  void *pop[2] = {nullptr, nullptr};
+  int32_t *phi[2] = {nullptr, nullptr};
+  float *u = nullptr;
+  float4 *frep = nullptr;
+  float *mom = nullptr;
+  double *stage = nullptr;
+  size_t stage_bytes = 0;
+  int32_t *partner = nullptr;
+  ReduceOut *red_part = nullptr, *red_out = nullptr;
+  int cur = 0;        // population buffer holding the current state
+  int pcur = 0;       // phi buffer holding phi^n
+  bool initialised = false;
+  long long steps = 0;
+  long long phi_q30_ref = 0;
+  // profiler
+  bool prof = false;
+  std::vector<ProfPair> pairs;
+  std::vector<cudaEvent_t> pool;
+  double prof_ms[LBM_K_COUNT] = {0};
+  int64_t prof_n[LBM_K_COUNT] = {0};
+};
+
+namespace {
+
+int from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return LBM_OK;
+  if (e == cudaErrorMemoryAllocation) return LBM_ERR_OOM;
+  return LBM_ERR_CUDA;
+}
+
+cudaEvent_t take_event(lbm_ctx *c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Wraps one launch in a pair of events when the profiler is on.
+template <class F> cudaError_t timed(lbm_ctx *c, int kind, F &&launch) {
+  if (!c->prof) return launch();
+  cudaEvent_t a = take_event(c), b = take_event(c);
+  if (!a || !b) return cudaErrorMemoryAllocation;
+  cudaEventRecord(a, c->stream);
+  cudaError_t e = launch();
+  cudaEventRecord(b, c->stream);
+  c->pairs.push_back({kind, a, b});
+  return e;
+}
+
+int validate(const lbm_params *p) {
+  if (!p) return LBM_ERR_ARG;
+  if (p->dim != 2 && p->dim != 3) return LBM_ERR_ARG;
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return LBM_ERR_ARG;
+  if (p->dim == 2 && (p->nz != 1 || p->Q != 9)) return LBM_ERR_ARG;
+  if (p->dim == 3 && p->Q != 19 && p->Q != 27) return LBM_ERR_ARG;
+  if (p->store < LBM_STORE_F32 || p->store > LBM_STORE_BF16) return LBM_ERR_ARG;
+  long long N = (long long)p->nx * p->ny * p->nz;
+  if (N > (long long)INT_MAX) return LBM_ERR_ARG;
+  if (!(p->rho_l > 0) || !(p->rho_g > 0) || !(p->nu_l > 0) || !(p->nu_g > 0)) return LBM_ERR_ARG;
+  if (!(p->eps > 0) || !(p->D >= 0) || !std::isfinite(p->sigma)) return LBM_ERR_ARG;
+  if (p->nci_on) {
+    if (p->w < 1 || p->w > 3) return LBM_ERR_ARG;
+    if (!(p->h0 > 0) || !(p->p > 0) || !(p->q_th > 0) || !(p->q_th <= 0.25)) return LBM_ERR_ARG;
+    if (!(p->eta >= 0) || !(p->eps_q > 0) || !std::isfinite(p->A_rep) || !std::isfinite(p->cos_opp))
+      return LBM_ERR_ARG;
+  }
+  if (!(p->eps_n > 0)) return LBM_ERR_ARG;
+  for (int a = 0; a < 3; a++)
+    if (!std::isfinite(p->g[a])) return LBM_ERR_ARG;
+  if (p->mass_check_every < 0 || !(p->mass_tol >= 0)) return LBM_ERR_ARG;
+  return LBM_OK;
+}
+
+void derive_kparams(const lbm_params &p, KParams &K) {
+  K.nx = p.nx; K.ny = p.ny; K.nz = p.nz;
+  K.N = (long long)p.nx * p.ny * p.nz;
+  K.rho_g = (float)p.rho_g;
+  K.drho = (float)(p.rho_l - p.rho_g);
+  K.mu_g = (float)(p.rho_g * p.nu_g);
+  K.dmu = (float)(p.rho_l * p.nu_l - p.rho_g * p.nu_g);
+  const double beta = 12.0 * p.sigma / p.eps, kap = 1.5 * p.sigma * p.eps;
+  K.beta4 = (float)(4.0 * beta);
+  K.kap = (float)kap;
+  K.rho_bar = (float)p.rho_l;
+  for (int a = 0; a < 3; a++) K.g[a] = (float)p.g[a];
+  K.nci_on = p.nci_on;
+  K.w = p.w;
+  K.A_rep = (float)p.A_rep; K.h0 = (float)p.h0; K.p = (float)p.p; K.q_th = (float)p.q_th;
+  K.eta = (float)p.eta; K.cos_opp = (float)p.cos_opp; K.eps_q = (float)p.eps_q; K.eps_n = (float)p.eps_n;
+  K.eps = (float)p.eps;
+  K.Dlap = (float)(p.D * 6.0);
+  K.kc = (float)(3.0 * 4.0 * p.D / p.eps);
+  K.rho_g64 = p.rho_g;
+  K.drho64 = p.rho_l - p.rho_g;
+}
+
+// Window offsets of Eq. 60 sorted by |r|^2, then by the canonical index
+// ((rz + w)(2w + 1) + (ry + w))(2w + 1) + (rx + w).
+void build_table(int dim, int w, NciTable &T) {
+  struct E { int d2, k, dx, dy, dz; };
+  std::vector<E> v;
+  const int W = 2 * w + 1, zr = dim == 3 ? w : 0;
+  for (int rz = -zr; rz <= zr; rz++)
+    for (int ry = -w; ry <= w; ry++)
+      for (int rx = -w; rx <= w; rx++) {
+        if (!rx && !ry && !rz) continue;
+        v.push_back({rx * rx + ry * ry + rz * rz, ((rz + zr) * W + (ry + w)) * W + (rx + w), rx, ry, rz});
+      }
+  std::sort(v.begin(), v.end(), [](const E &a, const E &b) { return a.d2 != b.d2 ? a.d2 < b.d2 : a.k < b.k; });
+  T.count = (int)v.size();
+  for (int i = 0; i < T.count; i++)
+    T.o[i] = NciOffset{(int8_t)v[i].dx, (int8_t)v[i].dy, (int8_t)v[i].dz, (int8_t)v[i].d2};
+}
+
+size_t store_size(int store) { return store == LBM_STORE_F32 ? 4 : 2; }
+
+int ensure_stage(lbm_ctx *c, size_t bytes) {
+  if (c->stage_bytes >= bytes) return LBM_OK;
+  if (c->stage) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->stage);
+    c->stage = nullptr;
+    c->stage_bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&c->stage, bytes);
+  if (e != cudaSuccess) {
+    c->stage = nullptr;
+    return from_cuda(e);
+  }
+  c->stage_bytes = bytes;
+  return LBM_OK;
+}
+
+int ensure_mom(lbm_ctx *c) {
+  if (c->mom) return LBM_OK;
+  cudaError_t e = cudaMalloc(&c->mom, sizeof(float) * 4 * c->N);
+  if (e != cudaSuccess) {
+    c->mom = nullptr;
+    return from_cuda(e);
+  }
+  return from_cuda(cudaMemsetAsync(c->mom, 0, sizeof(float) * 4 * c->N, c->stream));
+}
+
+int h2d(lbm_ctx *c, void *dst, const void *src, size_t bytes) {
+  return from_cuda(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+}
+int d2h(lbm_ctx *c, void *dst, const void *src, size_t bytes) {
+  return from_cuda(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream));
+}
+int sync(lbm_ctx *c) { return from_cuda(cudaStreamSynchronize(c->stream)); }
+
+// rho_bar from the exact phi sum; also records the phi-mass reference of the conservation check.
+int finish_init(lbm_ctx *c) {
+  int rc = from_cuda(launch_reduce(c->K, c->phi[c->pcur], c->u, c->red_part, c->red_out, c->stream));
+  if (rc) return rc;
+  ReduceOut r;
+  if ((rc = d2h(c, &r, c->red_out, sizeof(r)))) return rc;
+  if ((rc = sync(c))) return rc;
+  const double mean_phi = (double)r.phi_q30 / 1073741824.0 / (double)c->N;
+  c->K.rho_bar = (float)(c->P.rho_g + (c->P.rho_l - c->P.rho_g) * mean_phi);
+  c->phi_q30_ref = r.phi_q30;
+  c->initialised = true;
+  c->steps = 0;
+  return LBM_OK;
+}
+
+// Near-contact kernel + hydrodynamic kernel in moments mode on the current state -> c->mom.
+int run_moments(lbm_ctx *c) {
+  int rc = ensure_mom(c);
+  if (rc) return rc;
+  const int d = c->P.dim;
+  if (c->P.nci_on) {
+    rc = from_cuda(timed(c, LBM_K_NCI, [&] {
+      return launch_nci(d, c->K, c->T, c->phi[c->pcur], c->frep, nullptr, 0, c->stream);
+    }));
+    if (rc) return rc;
+  }
+  return from_cuda(timed(c, LBM_K_HYDRO, [&] {
+    return launch_hydro(c->P.Q, c->P.store, kMoments, c->K, c->pop[c->cur], nullptr, c->phi[c->pcur], c->frep,
+                        c->mom, c->mom + 3 * c->N, c->stream);
+  }));
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_params_default(lbm_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->dim = 3; p->nx = p->ny = p->nz = 64; p->Q = 19; p->store = LBM_STORE_F32;
+  p->rho_l = 1.0; p->rho_g = 1.0; p->nu_l = 0.005; p->nu_g = 0.05; p->sigma = 0.02;
+  p->eps = 4.0; p->D = 0.1;
+  p->nci_on = 1; p->w = 3; p->A_rep = 0.02; p->h0 = 1.0; p->p = 4.0;
+  p->q_th = 0.125; p->eta = 0.1; p->cos_opp = -0.8; p->eps_q = 1e-12; p->eps_n = 1e-12;
+  p->mass_check_every = 0; p->mass_tol = 1e-9;
+}
+
+int lbm_create(const lbm_params *p, lbm_ctx **out) {
+  if (!out) return LBM_ERR_ARG;
+  int rc = validate(p);
+  if (rc) return rc;
+  lbm_ctx *c = new (std::nothrow) lbm_ctx();
+  if (!c) return LBM_ERR_OOM;
+  c->P = *p;
+  derive_kparams(*p, c->K);
+  build_table(p->dim, p->nci_on ? p->w : 1, c->T);
+  c->N = c->K.N;
+  c->pop_bytes = (size_t)p->Q * (size_t)c->N * store_size(p->store);
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaMalloc(&c->pop[0], c->pop_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&c->pop[1], c->pop_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&c->phi[0], sizeof(int32_t) * c->N);
+  if (e == cudaSuccess) e = cudaMalloc(&c->phi[1], sizeof(int32_t) * c->N);
+  if (e == cudaSuccess) e = cudaMalloc(&c->u, sizeof(float) * 3 * c->N);
+  if (e == cudaSuccess) e = cudaMalloc(&c->frep, sizeof(float4) * c->N);
+  if (e == cudaSuccess) e = cudaMalloc(&c->red_part, sizeof(ReduceOut) * kReduceBlocks);
+  if (e == cudaSuccess) e = cudaMalloc(&c->red_out, sizeof(ReduceOut));
+  if (e == cudaSuccess) e = cudaMemset(c->u, 0, sizeof(float) * 3 * c->N);
+  if (e == cudaSuccess) e = cudaMemset(c->frep, 0, sizeof(float4) * c->N);
+  if (e == cudaSuccess) e = cudaMemset(c->phi[0], 0, sizeof(int32_t) * c->N);
+  if (e == cudaSuccess) e = cudaMemset(c->phi[1], 0, sizeof(int32_t) * c->N);
+  if (e != cudaSuccess) {
+    lbm_destroy(c);
+    return from_cuda(e);
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);  // the stream must outlive the context
+  for (auto &pp : c->pairs) {
+    cudaEventDestroy(pp.a);
+    cudaEventDestroy(pp.b);
+  }
+  for (auto e : c->pool) cudaEventDestroy(e);
+  cudaFree(c->pop[0]); cudaFree(c->pop[1]);
+  cudaFree(c->phi[0]); cudaFree(c->phi[1]);
+  cudaFree(c->u); cudaFree(c->frep); cudaFree(c->mom); cudaFree(c->stage);
+  cudaFree(c->partner); cudaFree(c->red_part); cudaFree(c->red_out);
+  delete c;
+}
+
+int lbm_set_stream(lbm_ctx *c, void *stream) {
+  if (!c) return LBM_ERR_ARG;
+  c->stream = (cudaStream_t)stream;
+  return LBM_OK;
+}
+
+int lbm_init_fields(lbm_ctx *c, const double *phi, const double *u, const double *pstar) {
+  if (!c || !phi || !u) return LBM_ERR_ARG;
+  const long long N = c->N;
+  int rc = ensure_stage(c, sizeof(double) * 5 * N);
+  if (rc) return rc;
+  double *s_phi = c->stage, *s_u = c->stage + N, *s_ps = c->stage + 4 * N;
+  if ((rc = h2d(c, s_phi, phi, sizeof(double) * N))) return rc;
+  if ((rc = h2d(c, s_u, u, sizeof(double) * 3 * N))) return rc;
+  if (pstar && (rc = h2d(c, s_ps, pstar, sizeof(double) * N))) return rc;
+  c->cur = 0;
+  c->pcur = 0;
+  rc = from_cuda(timed(c, LBM_K_CONVERT, [&] { return launch_phi_in(c->K, s_phi, c->phi[0], c->stream); }));
+  if (rc) return rc;
+  rc = from_cuda(timed(c, LBM_K_CONVERT, [&] {
+    return launch_init_pops(c->P.Q, c->P.store, c->K, s_u, pstar ? s_ps : nullptr, c->pop[0], c->stream);
+  }));
+  if (rc) return rc;
+  return finish_init(c);
+}
+
+int lbm_set_state(lbm_ctx *c, const double *f, const double *phi) {
+  if (!c || !f || !phi) return LBM_ERR_ARG;
+  const long long N = c->N;
+  const int Q = c->P.Q;
+  int rc = ensure_stage(c, sizeof(double) * (size_t)(Q + 1) * N);
+  if (rc) return rc;
+  double *s_f = c->stage, *s_phi = c->stage + (size_t)Q * N;
+  if ((rc = h2d(c, s_f, f, sizeof(double) * (size_t)Q * N))) return rc;
+  if ((rc = h2d(c, s_phi, phi, sizeof(double) * N))) return rc;
+  c->cur = 0;
+  c->pcur = 0;
+  rc = from_cuda(timed(c, LBM_K_CONVERT, [&] { return launch_phi_in(c->K, s_phi, c->phi[0], c->stream); }));
+  if (rc) return rc;
+  rc = from_cuda(timed(c, LBM_K_CONVERT, [&] { return launch_set_pops(Q, c->P.store, c->K, s_f, c->pop[0], c->stream); }));
+  if (rc) return rc;
+  return finish_init(c);
+}
+
+int lbm_get_state(lbm_ctx *c, double *f, double *phi) {
+  if (!c) return LBM_ERR_ARG;
+  if (!c->initialised) return LBM_ERR_STATE;
+  const long long N = c->N;
+  const int Q = c->P.Q;
+  int rc = ensure_stage(c, sizeof(double) * (size_t)(Q + 1) * N);
+  if (rc) return rc;
+  double *s_f = c->stage, *s_phi = c->stage + (size_t)Q * N;
+  if (f) {
+    rc = from_cuda(timed(c, LBM_K_CONVERT, [&] { return launch_get_pops(Q, c->P.store, c->K, c->pop[c->cur], s_f, c->stream); }));
+    if (rc) return rc;
+    if ((rc = d2h(c, f, s_f, sizeof(double) * (size_t)Q * N))) return rc;
+  }
+  if (phi) {
+    rc = from_cuda(timed(c, LBM_K_CONVERT, [&] { return launch_phi_out(c->K, c->phi[c->pcur], s_phi, c->stream); }));
+    if (rc) return rc;
+    if ((rc = d2h(c, phi, s_phi, sizeof(double) * N))) return rc;
+  }
+  return sync(c);
+}
+
+int lbm_step(lbm_ctx *c, int n) {
+  if (!c || n < 0) return LBM_ERR_ARG;
+  if (!c->initialised) return LBM_ERR_STATE;
+  const int d = c->P.dim;
+  for (int s = 0; s < n; s++) {
+    const int nxt = c->cur ^ 1, pn = c->pcur ^ 1;
+    int rc;
+    if (c->P.nci_on) {
+      rc = from_cuda(timed(c, LBM_K_NCI, [&] {
+        return launch_nci(d, c->K, c->T, c->phi[c->pcur], c->frep, nullptr, 0, c->stream);
+      }));
+      if (rc) return rc;
+    }
+    rc = from_cuda(timed(c, LBM_K_HYDRO, [&] {
+      return launch_hydro(c->P.Q, c->P.store, kStep, c->K, c->pop[c->cur], c->pop[nxt], c->phi[c->pcur], c->frep,
+                          c->u, nullptr, c->stream);
+    }));
+    if (rc) return rc;
+    rc = from_cuda(timed(c, LBM_K_PHASE, [&] { return launch_phase(d, c->K, c->phi[c->pcur], c->u, c->phi[pn], c->stream); }));
+    if (rc) return rc;
+    c->cur = nxt;
+    c->pcur = pn;
+    c->steps++;
+    if (c->P.mass_check_every > 0 && c->steps % c->P.mass_check_every == 0) {
+      rc = from_cuda(timed(c, LBM_K_REDUCE, [&] {
+        return launch_reduce(c->K, c->phi[c->pcur], c->u, c->red_part, c->red_out, c->stream);
+      }));
+      if (rc) return rc;
+      ReduceOut r;
+      if ((rc = d2h(c, &r, c->red_out, sizeof(r)))) return rc;
+      if ((rc = sync(c))) return rc;
+      const double ref = std::fabs((double)c->phi_q30_ref);
+      const double drift = std::fabs((double)(r.phi_q30 - c->phi_q30_ref)) / (ref > 0 ? ref : 1.0);
+      if (r.nonfinite > 0 || !(drift <= c->P.mass_tol)) return LBM_ERR_UNSTABLE;
+    }
+  }
+  return LBM_OK;
+}
+
+int lbm_read_fields(lbm_ctx *c, double *phi, double *u, double *pstar) {
+  if (!c) return LBM_ERR_ARG;
+  if (!c->initialised) return LBM_ERR_STATE;
+  const long long N = c->N;
+  int rc = ensure_stage(c, sizeof(double) * 5 * N);
+  if (rc) return rc;
+  if (u || pstar) {
+    if ((rc = run_moments(c))) return rc;
+  }
+  if (phi) {
+    rc = from_cuda(timed(c, LBM_K_CONVERT, [&] { return launch_phi_out(c->K, c->phi[c->pcur], c->stage, c->stream); }));
+    if (rc) return rc;
+    if ((rc = d2h(c, phi, c->stage, sizeof(double) * N))) return rc;
+  }
+  if (u) {
+    rc = from_cuda(timed(c, LBM_K_CONVERT, [&] { return launch_f32_out(3 * N, c->mom, c->stage + N, c->stream); }));
+    if (rc) return rc;
+    if ((rc = d2h(c, u, c->stage + N, sizeof(double) * 3 * N))) return rc;
+  }
+  if (pstar) {
+    rc = from_cuda(timed(c, LBM_K_CONVERT, [&] { return launch_f32_out(N, c->mom + 3 * N, c->stage + 4 * N, c->stream); }));
+    if (rc) return rc;
+    if ((rc = d2h(c, pstar, c->stage + 4 * N, sizeof(double) * N))) return rc;
+  }
+  return sync(c);
+}
+
+int lbm_mass(lbm_ctx *c, double *phi_mass, double *mom) {
+  if (!c) return LBM_ERR_ARG;
+  if (!c->initialised) return LBM_ERR_STATE;
+  int rc = run_moments(c);
+  if (rc) return rc;
+  rc = from_cuda(timed(c, LBM_K_REDUCE, [&] {
+    return launch_reduce(c->K, c->phi[c->pcur], c->mom, c->red_part, c->red_out, c->stream);
+  }));
+  if (rc) return rc;
+  ReduceOut r;
+  if ((rc = d2h(c, &r, c->red_out, sizeof(r)))) return rc;
+  if ((rc = sync(c))) return rc;
+  if (phi_mass) *phi_mass = (double)r.phi_q30 / 1073741824.0;
+  if (mom)
+    for (int a = 0; a < 3; a++) mom[a] = r.mom[a];
+  return LBM_OK;
+}
+
+int lbm_read_nci(lbm_ctx *c, int32_t *partner, double *frep) {
+  if (!c) return LBM_ERR_ARG;
+  if (!c->initialised) return LBM_ERR_STATE;
+  const long long N = c->N;
+  int rc;
+  if (!c->partner) {
+    cudaError_t e = cudaMalloc(&c->partner, sizeof(int32_t) * 3 * N);
+    if (e != cudaSuccess) {
+      c->partner = nullptr;
+      return from_cuda(e);
+    }
+  }
+  if ((rc = ensure_stage(c, sizeof(double) * 3 * N))) return rc;
+  rc = from_cuda(timed(c, LBM_K_NCI, [&] {
+    return launch_nci(c->P.dim, c->K, c->T, c->phi[c->pcur], c->frep, c->partner, 1, c->stream);
+  }));
+  if (rc) return rc;
+  if (partner && (rc = d2h(c, partner, c->partner, sizeof(int32_t) * 3 * N))) return rc;
+  if (frep) {
+    rc = from_cuda(timed(c, LBM_K_CONVERT, [&] { return launch_partner_frep_out(c->K, c->P.dim, c->frep, c->stage, c->stream); }));
+    if (rc) return rc;
+    if ((rc = d2h(c, frep, c->stage, sizeof(double) * 3 * N))) return rc;
+  }
+  return sync(c);
+}
+
+int lbm_synchronize(lbm_ctx *c) {
+  if (!c) return LBM_ERR_ARG;
+  return sync(c);
+}
+
+int lbm_profile(lbm_ctx *c, int enable) {
+  if (!c) return LBM_ERR_ARG;
+  int rc = sync(c);
+  if (rc) return rc;
+  for (auto &pp : c->pairs) {
+    c->pool.push_back(pp.a);
+    c->pool.push_back(pp.b);
+  }
+  c->pairs.clear();
+  for (int k = 0; k < LBM_K_COUNT; k++) {
+    c->prof_ms[k] = 0;
+    c->prof_n[k] = 0;
+  }
+  c->prof = enable != 0;
+  return LBM_OK;
+}
+
+int lbm_profile_read(lbm_ctx *c, double *ms, int64_t *launches) {
+  if (!c) return LBM_ERR_ARG;
+  int rc = sync(c);
+  if (rc) return rc;
+  for (auto &pp : c->pairs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, pp.a, pp.b) == cudaSuccess) c->prof_ms[pp.kind] += t;
+    c->prof_n[pp.kind] += 1;
+    c->pool.push_back(pp.a);
+    c->pool.push_back(pp.b);
+  }
+  c->pairs.clear();
+  for (int k = 0; k < LBM_K_COUNT; k++) {
+    if (ms) ms[k] = c->prof_ms[k];
+    if (launches) launches[k] = c->prof_n[k];
+  }
+  return LBM_OK;
+}
+
+int lbm_lattice(int dim, int Q, int *c, double *w) {
+  if (!c || !w) return LBM_ERR_ARG;
+  auto fill = [&](auto L) {
+    using LT = decltype(L);
+    for (int i = 0; i < LT::Q; i++) {
+      for (int a = 0; a < 3; a++) c[3 * i + a] = LT::c(i, a);
+      w[i] = LT::wd(i);
+    }
+  };
+  if (dim == 2 && Q == 9) fill(D2Q9{});
+  else if (dim == 3 && Q == 19) fill(D3Q19{});
+  else if (dim == 3 && Q == 27) fill(D3Q27{});
+  else return LBM_ERR_ARG;
+  return LBM_OK;
+}
+
+const char *lbm_strerror(int s) {
+  switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_ARG: return "invalid argument";
+    case LBM_ERR_OOM: return "device out of memory";
+    case LBM_ERR_CUDA: return "CUDA runtime error";
+    case LBM_ERR_UNSTABLE: return "unstable: non-finite velocity or phi-mass drift above tolerance";
+    case LBM_ERR_STATE: return "call out of order (no state initialised)";
+    default: return "unknown status";
+  }
+}
+
+const char *lbm_kernel_name(int kind) {
+  switch (kind) {
+    case LBM_K_NCI: return "nci";
+    case LBM_K_HYDRO: return "hydro";
+    case LBM_K_PHASE: return "phase";
+    case LBM_K_REDUCE: return "reduce";
+    case LBM_K_CONVERT: return "convert";
+    default: return "unknown";
+  }
+}
+
+}  // extern "C"

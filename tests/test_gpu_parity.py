@@ -1,0 +1,253 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle on identical seeded
+inputs. Tolerances: single step (identical input) 1e-6 on populations and velocities, 1e-7 on
+phi; trajectories max|dphi| <= 1e-5 and max|du| <= 1e-6 after 200 steps; near-contact decisions
+identical except at cells whose oracle decision margin is below 1e-5."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2603_17481_gb300 import binding as B
+from paper_2603_17481_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2603_17481_gb300 import build
+    build.build()
+    O.build()
+    torch.cuda.set_device(0)
+    return True
+
+
+def _random_state(cfg, seed, f_noise=2e-3):
+    phi, u = W.smooth_random_fields(cfg, seed=seed)
+    phi = W.to_q30_grid(phi)
+    P = O.make_params(cfg)
+    N = W.ncells(cfg)
+    ps = W.noise(N, seed + 1, 5e-3)
+    f = O.init(P, phi, u, pstar=ps)
+    _, w = O.lattice(cfg["dim"], cfg["Q"])
+    f = f + f_noise * w[:, None] * W.noise((cfg["Q"], N), seed + 2)
+    return P, phi, u, f
+
+
+def _compare_nci(sim, P, phi, tol_margin=1e-5):
+    part_g, frep_g = sim.read_nci()
+    part_o, frep_o, marg = O.nci(P, phi)
+    chi_o = part_o[:, 0] != O.NO_PARTNER
+    diff = np.any(part_g != part_o, axis=1)
+    assert np.all(marg[diff] < tol_margin), f"{diff.sum()} partner mismatches at robust cells"
+    ok = ~diff
+    scale = max(np.max(np.abs(frep_o)), 1e-30)
+    assert np.max(np.abs(frep_g[:, ok] - frep_o[:, ok])) <= 2e-5 * scale
+    return int(chi_o.sum()), int(diff.sum())
+
+
+CASES_1STEP = [
+    (3, 19, (37, 21, 13), 11, "f32"),
+    (3, 27, (35, 19, 11), 12, "f32"),
+    (2, 9, (45, 27, 1), 13, "f32"),
+    (3, 19, (8, 8, 8), 14, "f32"),
+    (3, 19, (64, 12, 9), 15, "f32"),
+]
+
+
+@pytest.mark.parametrize("dim,Q,shape,seed,store", CASES_1STEP)
+def test_single_step_identical_input(dim, Q, shape, seed, store):
+    """One step from a random non-equilibrium state with two nearly touching droplets: near-contact
+    partners and force, velocity moments, post-step populations and phi, on ragged tile counts."""
+    cfg = W.base_config(dim, *shape, Q, rho_g=0.1)
+    P, phi, u, f = _random_state(cfg, seed)
+    sim = B.Lbm(cfg, store=store)
+    sim.set_state(f, phi)
+    nchi, nmis = _compare_nci(sim, P, phi)
+    assert nchi > 0
+    _, ug, psg = sim.read_fields()
+    pso, uo = O.moments(P, f, phi)
+    assert np.max(np.abs(ug - uo)) < 1e-6
+    assert np.max(np.abs(psg - pso)) < 1e-6
+    sim.step(1)
+    fg, phg = sim.get_state()
+    fo, pho, _ = O.step(P, f, phi, 1)
+    assert np.max(np.abs(fg - fo)) < 1e-6
+    assert np.max(np.abs(phg - pho)) < 1e-7
+    m0 = np.round(phi * 2 ** 30).sum()
+    assert np.round(phg * 2 ** 30).sum() == m0  # exact fixed-point conservation
+
+
+def test_c1_head_on_2d_200_steps():
+    """2D head-on collision (128x64 D2Q9), 200 steps: max|dphi| <= 1e-5, max|du| <= 1e-6."""
+    cfg, phi, u = W.c1_head_on_2d()
+    phi = W.to_q30_grid(phi)
+    P = O.make_params(cfg)
+    f = O.init(P, phi, u)
+    fo, pho, _ = O.step(P, f, phi, 200)
+    _, uo = O.moments(P, fo, pho)
+    sim = B.Lbm(cfg)
+    sim.init_fields(phi, u)
+    sim.step(200)
+    phg, ug, _ = sim.read_fields()
+    assert np.max(np.abs(phg - pho)) <= 1e-5
+    assert np.max(np.abs(ug - uo)) <= 1e-6
+
+
+def test_c1_contact_phase_400_steps():
+    """The same collision through its near-contact phase (the repulsion switches on near step
+    250): partners compared at step 400, and fields within 1e-5 (phi) / 1e-6 (u)."""
+    cfg, phi, u = W.c1_head_on_2d()
+    phi = W.to_q30_grid(phi)
+    P = O.make_params(cfg)
+    f = O.init(P, phi, u)
+    fo, pho, _ = O.step(P, f, phi, 400)
+    _, uo = O.moments(P, fo, pho)
+    sim = B.Lbm(cfg)
+    sim.init_fields(phi, u)
+    sim.step(400)
+    phg, ug, _ = sim.read_fields()
+    part_g, _ = sim.read_nci()
+    part_o, _, _ = O.nci(P, pho)
+    assert (part_o[:, 0] != O.NO_PARTNER).sum() > 0
+    assert np.max(np.abs(phg - pho)) <= 1e-5
+    assert np.max(np.abs(ug - uo)) <= 1e-6
+
+
+def test_c2_offcentre_3d_200_steps():
+    """3D off-centre collision (128x64x64 D3Q19, ratio 10, seeded impact offset), 200 steps:
+    max|dphi| <= 1e-5, max|du| <= 1e-6."""
+    cfg, phi, u = W.c2_offcentre_3d()
+    phi = W.to_q30_grid(phi)
+    P = O.make_params(cfg)
+    f = O.init(P, phi, u)
+    fo, pho, _ = O.step(P, f, phi, 200)
+    _, uo = O.moments(P, fo, pho)
+    sim = B.Lbm(cfg)
+    sim.init_fields(phi, u)
+    sim.step(200)
+    phg, ug, _ = sim.read_fields()
+    assert np.max(np.abs(phg - pho)) <= 1e-5
+    assert np.max(np.abs(ug - uo)) <= 1e-6
+
+
+@pytest.mark.parametrize("store,tol", [("f16", 1e-3), ("bf16", 1e-2)])
+def test_half_precision_store_phi_error_and_mass(store, tol):
+    """Populations stored as FP16/BF16 (f/w_i) with FP32 arithmetic, ratio-100 collision
+    (128x64x64, R = 12), 200 steps: phi error against the FP64 oracle below tol, phi mass exact."""
+    cfg, phi, u = W.c3_head_on_3d(nx=128, ny=64, nz=64, R=12.0)
+    phi = W.to_q30_grid(phi)
+    P = O.make_params(cfg)
+    f = O.init(P, phi, u)
+    fo, pho, _ = O.step(P, f, phi, 200)
+    sim = B.Lbm(cfg, store=store)
+    sim.init_fields(phi, u)
+    m0, _ = sim.mass()
+    sim.step(200)
+    m1, _ = sim.mass()
+    phg, _, _ = sim.read_fields(want=("phi",))
+    assert np.max(np.abs(phg - pho)) <= tol
+    assert abs(m1 - m0) <= 1e-12 * abs(m0)
+
+
+def test_mass_and_momentum_reductions():
+    """lbm_mass: sum(phi) equals the FP64 sum of the read-back phi; sum(rho u) equals the FP64
+    sum from the read-back fields."""
+    cfg = W.base_config(3, 33, 17, 12, 19, rho_g=0.1)
+    P, phi, u, f = _random_state(cfg, 5)
+    sim = B.Lbm(cfg)
+    sim.set_state(f, phi)
+    sim.step(3)
+    m, mom = sim.mass()
+    phg, ug, _ = sim.read_fields()
+    rho = cfg["rho_g"] + (cfg["rho_l"] - cfg["rho_g"]) * phg
+    assert abs(m - phg.sum()) <= 1e-12 * abs(m)
+    assert np.max(np.abs(mom - (rho * ug).sum(axis=1))) <= 1e-9
+
+
+def test_zero_steps_and_state_roundtrip():
+    cfg = W.base_config(3, 20, 12, 9, 27)
+    P, phi, u, f = _random_state(cfg, 8)
+    sim = B.Lbm(cfg)
+    sim.set_state(f, phi)
+    sim.step(0)
+    fg, phg = sim.get_state()
+    assert np.max(np.abs(fg - f)) < 1e-7 * np.max(np.abs(f)) + 1e-12
+    assert np.array_equal(phg, phi)
+
+
+def test_nci_off_and_single_phase():
+    """Degenerate cases: repulsion off (chi read-back empty when nothing is near), uniform phi
+    (no interface: forces vanish) keeps a uniform flow exactly uniform."""
+    cfg = W.base_config(3, 16, 8, 8, 19, nci_on=0)
+    N = W.ncells(cfg)
+    phi = np.ones(N)
+    u = np.zeros((3, N))
+    u[0] = 0.03
+    sim = B.Lbm(cfg)
+    sim.init_fields(phi, u)
+    sim.step(10)
+    phg, ug, psg = sim.read_fields()
+    assert np.max(np.abs(ug[0] - 0.03)) < 1e-7
+    assert np.max(np.abs(ug[1:])) < 1e-7
+    assert np.array_equal(phg, phi)
+
+
+def test_step_before_init_and_nan_detection():
+    cfg = W.base_config(3, 16, 8, 8, 19)
+    sim = B.Lbm(cfg, mass_check_every=1)
+    with pytest.raises(B.LbmError) as ei:
+        sim.step(1)
+    assert ei.value.code == B.LBM_ERR_STATE
+    N = W.ncells(cfg)
+    phi, u = W.droplet_fields(cfg, [(8, 4, 4)], [3.0], [(0, 0, 0)])
+    u[0, 5] = np.nan  # injected on the host: the periodic check must report it
+    sim.init_fields(phi, u)
+    with pytest.raises(B.LbmError) as ei:
+        sim.step(2)
+    assert ei.value.code == B.LBM_ERR_UNSTABLE
+
+
+def test_full_size_single_step_c3():
+    """The benchmark's launch configuration (256x128x128 D3Q19, ratio 100): one step from the
+    initial state against the oracle on the whole grid."""
+    cfg, phi, u = W.c3_head_on_3d()
+    phi = W.to_q30_grid(phi)
+    P = O.make_params(cfg)
+    f = O.init(P, phi, u)
+    fo, pho, _ = O.step(P, f, phi, 1)
+    sim = B.Lbm(cfg)
+    sim.init_fields(phi, u)
+    sim.step(1)
+    fg, phg = sim.get_state()
+    assert np.max(np.abs(fg - fo)) < 1e-6
+    assert np.max(np.abs(phg - pho)) < 1e-7
+
+
+@pytest.mark.slow
+def test_c2_centroids_after_2000_steps():
+    """Droplet centroids (phi-weighted, per half-domain in x) within 0.05 cells after 2000 steps."""
+    cfg, phi, u = W.c2_offcentre_3d()
+    phi = W.to_q30_grid(phi)
+    P = O.make_params(cfg)
+    f = O.init(P, phi, u)
+    fo, pho, _ = O.step(P, f, phi, 2000)
+    sim = B.Lbm(cfg)
+    sim.init_fields(phi, u)
+    sim.step(2000)
+    phg, _, _ = sim.read_fields(want=("phi",))
+
+    def centroids(ph):
+        nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+        g = ph.reshape(nz, ny, nx)
+        out = []
+        for sl in (slice(0, nx // 2), slice(nx // 2, nx)):
+            m = g[:, :, sl]
+            zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx)[sl], indexing="ij")
+            out.append([(m * xx).sum() / m.sum(), (m * yy).sum() / m.sum(), (m * zz).sum() / m.sum()])
+        return np.array(out)
+
+    assert np.max(np.abs(centroids(phg) - centroids(pho))) <= 0.05
