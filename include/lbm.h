@@ -78,7 +78,7 @@ typedef struct {
   double q_th;        /* interfacial gate (Eq. 59; paper 0.125)                                 */
   double eta;         /* iso-interface tolerance (Eq. 61; paper 0.1)                            */
   double cos_opp;     /* facing threshold (Eq. 62; paper -0.8)                                  */
-  double eps_q, eps_n;/* floors of Eqs. 67 and 57                                               */
+  double eps_q, eps_n;/* floors of Eq. 67 and of the normal grad/(|grad| + eps_n), Eqs. 25, 57  */
   double g[3];        /* body acceleration; F_ext = (rho - rho_bar) g, rho_bar = mean initial rho */
   int mass_check_every; /* lbm_step runs the FP64 phi-mass / NaN check every this many steps; 0 = off */
   double mass_tol;    /* relative phi-mass drift that makes the check fail                      */

@@ -233,7 +233,7 @@ void lbm_params_default(lbm_params *p) {
   p->rho_l = 1.0; p->rho_g = 1.0; p->nu_l = 0.005; p->nu_g = 0.05; p->sigma = 0.02;
   p->eps = 4.0; p->D = 0.1;
   p->nci_on = 1; p->w = 3; p->A_rep = 0.02; p->h0 = 1.0; p->p = 4.0;
-  p->q_th = 0.125; p->eta = 0.1; p->cos_opp = -0.8; p->eps_q = 1e-12; p->eps_n = 1e-12;
+  p->q_th = 0.125; p->eta = 0.1; p->cos_opp = -0.8; p->eps_q = 1e-12; p->eps_n = 1e-4;
   p->mass_check_every = 0; p->mass_tol = 1e-9;
 }
 

@@ -15,9 +15,13 @@ import math
 import numpy as np
 
 #: Near-contact detection and force parameters printed in Sec. 2.3.2 (w, q_th, eta, cos_opp) and
-#: Sec. 2.2.6 / Eq. 71 (h0 = 1 lattice unit, p = 4); eps_q and eps_n are small floors.
+#: Sec. 2.2.6 / Eq. 71 (h0 = 1 lattice unit, p = 4). eps_q is a small floor. eps_n, the
+#: regularisation of the normal grad(phi) / (|grad(phi)| + eps_n) (Eq. 57, also used for the
+#: compressive normal of Eq. 25), is not given in the paper: 1e-4 keeps the normal well defined
+#: where |grad(phi)| is round-off (bulk regions with phi slightly off 0 or 1), while changing it by
+#: at most 0.1 % in the interfacial band where |grad(phi)| >= 0.1.
 PAPER_NCI = dict(nci_on=1, w=3, q_th=0.125, eta=0.1, cos_opp=-0.8, h0=1.0, p=4.0,
-                 eps_q=1e-12, eps_n=1e-12)
+                 eps_q=1e-12, eps_n=1e-4)
 
 Q30 = float(1 << 30)
 

@@ -50,7 +50,7 @@ def test_w_h_values(orc):
 
 
 def _film_cfg(ratio=10.0, decide_f32=0):
-    cfg = W.base_config(3, 24, 8, 8, 19, rho_g=1.0 / ratio, decide_f32=decide_f32)
+    cfg = W.base_config(3, 24, 8, 8, 19, rho_g=1.0 / ratio, decide_f32=decide_f32, eps_n=1e-12)
     return cfg
 
 
