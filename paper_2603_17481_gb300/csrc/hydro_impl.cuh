@@ -5,8 +5,10 @@
 // Layout: populations are structure-of-arrays, buf[i * N + n]. The buffer read at step t holds
 // post-collision populations of step t-1 at their source cell, so the pre-collision population
 // of direction i at cell x is src[i][x - c_i] (pull); the kernel writes dst[i][x] = f_post_i(x).
-// One thread per cell; phi of the tile + 1 halo is staged in shared memory as fixed-point
-// integers so that every stencil difference is exact before conversion to FP32.
+// One thread per cell, 32 consecutive x per warp (coalesced stores, loads offset by one cell).
+// Each thread wraps its neighbour coordinates once per axis and forms the 9 (3D) or 3 (2D) row
+// offsets of its neighbourhood, so a pull address is one add. phi of the tile + 1 halo is staged
+// in shared memory row by row as fixed-point integers; stencil differences are exact integers.
 //
 // The collision is evaluated from moments rather than by summing over tensors: with the
 // fourth-order isotropy of D2Q9/D3Q19/D3Q27, sum f_eq c c = p* cs^2 I + u u and sum S c c =
@@ -15,6 +17,12 @@
 //   H2 : T   = c.T.c - cs^2 tr T,
 //   H3 : uuu = (c.u)^3 - 3 cs^2 |u|^2 (c.u),
 //   H3 : A3  = 3 (c.u)(c.A2.c) - 3 cs^2 [ (c.u) tr A2 + 2 c.A2.u ]   (A3 of Eq. 16).
+// With cs^2 = 1/3 the post-collision population f_eq + (1 - omega) Reg + S/2 is, per direction,
+//   f_i / w_i = E(c) + O(c),  f_{-i} / w_i = E(c) - O(c),
+//   E = C0 + 4.5 (c.u)^2 + 4.5 (1-omega) c.A2.c + 4.5 (c.u)(c.F'),
+//   O = (c.u) C1 + 4.5 (c.u)^3 + 13.5 (1-omega)(c.u)(c.A2.c) - 9 (1-omega) c.A2.u + 1.5 c.F',
+//   C0 = p* - 1.5 |u|^2 - 1.5 (1-omega) tr A2 - 1.5 u.F',  C1 = 3 - 4.5 |u|^2 - 4.5 (1-omega) tr A2,
+// so each pair of opposite directions shares its even and odd parts.
 #pragma once
 
 #include "launch.h"
@@ -22,43 +30,63 @@
 namespace lbm {
 
 template <class L, int S, int MODE>
-__global__ void __launch_bounds__(Tile<L::D>::X * Tile<L::D>::Y * Tile<L::D>::Z)
+__global__ void __launch_bounds__(Tile<L::D>::X * Tile<L::D>::Y * Tile<L::D>::Z, 4)
 k_hydro(const KParams P, const typename Store<S>::T *__restrict__ src, typename Store<S>::T *__restrict__ dst,
         const int32_t *__restrict__ phi, const float4 *__restrict__ frep, float *__restrict__ u_out,
-        float *__restrict__ ps_out) {
+        float *__restrict__ ps_out, int *__restrict__ reset) {
   constexpr int DIM = L::D;
   using SL = typename StencilOf<DIM>::type;
   using TT = Tile<DIM>;
+  static_assert(TT::X == 32, "one warp per x row");
   constexpr int HX = TT::X + 2, HY = TT::Y + 2, HZ = DIM == 3 ? TT::Z + 2 : 1;
-  constexpr int NB = HX * HY * HZ, NT = TT::X * TT::Y * TT::Z;
-  __shared__ int32_t s_phi[NB];
+  constexpr int NROWS = HY * HZ, NWARPS = TT::Y * TT::Z;
+  __shared__ int32_t s_phi[NROWS * HX];
 
   const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
-  const int tid = tx + TT::X * (ty + TT::Y * tz);
-  const int x0 = blockIdx.x * TT::X, y0 = blockIdx.y * TT::Y, z0 = blockIdx.z * TT::Z;
   const int nx = P.nx, ny = P.ny, nz = P.nz;
-  for (int t = tid; t < NB; t += NT) {
-    int bx = t % HX, by = (t / HX) % HY, bz = t / (HX * HY);
-    int X = wrapi(x0 + bx - 1, nx), Y = wrapi(y0 + by - 1, ny), Z = DIM == 3 ? wrapi(z0 + bz - 1, nz) : 0;
-    s_phi[t] = phi[(long long)X + (long long)nx * (Y + (long long)ny * Z)];
+  const int x0 = blockIdx.x * TT::X, y0 = blockIdx.y * TT::Y, z0 = blockIdx.z * TT::Z;
+  // the near-contact tile list of this phi has been consumed: clear its count for reuse
+  if (reset && (blockIdx.x | blockIdx.y | blockIdx.z | tx | ty | tz) == 0) *reset = 0;
+
+  // stage phi (tile + 1 halo): warp w loads rows w, w + NWARPS, ...
+  {
+    const int xl = wrapn(x0 - 1 + tx, nx);
+    const int xr = wrapn(x0 + 31 + (tx & 1), nx);
+    for (int r = ty + TT::Y * tz; r < NROWS; r += NWARPS) {
+      const int ry = r % HY, rz = r / HY;
+      const int Y = wrapn(y0 + ry - 1, ny);
+      const int Z = DIM == 3 ? wrapn(z0 + rz - 1, nz) : 0;
+      const int32_t *row = phi + (long long)nx * (Y + (long long)ny * Z);
+      s_phi[r * HX + tx] = row[xl];
+      if (tx < 2) s_phi[r * HX + 32 + tx] = row[xr];
+    }
   }
   __syncthreads();
 
   const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
   if (x >= nx || y >= ny || z >= nz) return;
-  const long long N = P.N;
-  const long long idx = (long long)x + (long long)nx * (y + (long long)ny * z);
+  const int N = (int)P.N;
 
-  // pull: f_i(x) = src_i(x - c_i), periodic
+  // wrapped neighbour coordinates and row offsets rb[cy+1][cz+1]
+  int X[3], RB[3][3];
+  X[0] = x == 0 ? nx - 1 : x - 1; X[1] = x; X[2] = x == nx - 1 ? 0 : x + 1;
+  {
+    const int Y[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
+    int Z[3] = {0, 0, 0};
+    if (DIM == 3) { Z[0] = z == 0 ? nz - 1 : z - 1; Z[1] = z; Z[2] = z == nz - 1 ? 0 : z + 1; }
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+      for (int b = 0; b < 3; b++) RB[a][b] = nx * (Y[a] + ny * Z[b]);
+  }
+  const int idx = x + RB[1][1];
+
+  // pull: f_i(x) = src_i(x - c_i)
   float f[L::Q];
 #pragma unroll
   for (int i = 0; i < L::Q; i++) {
-    int sx = x - L::c(i, 0), sy = y - L::c(i, 1), sz = z - L::c(i, 2);
-    sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
-    sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
-    if (DIM == 3) sz = sz < 0 ? sz + nz : (sz >= nz ? sz - nz : sz);
-    const long long sidx = (long long)sx + (long long)nx * (sy + (long long)ny * sz);
-    f[i] = Store<S>::ld(src + (long long)i * N + sidx, L::w(i));
+    const int s = X[1 - L::c(i, 0)] + RB[1 - L::c(i, 1)][1 - L::c(i, 2)];
+    f[i] = Store<S>::ld(src + (long long)i * N + s, L::w(i));
   }
 
   // isotropic gradient and Laplacian of phi (Eqs. 22-23) on exact fixed-point differences
@@ -82,10 +110,10 @@ k_hydro(const KParams P, const typename Store<S>::T *__restrict__ src, typename 
 
   // mixture properties, Eqs. 8-10 (linear rho and mu)
   const float rho = P.rho_g + P.drho * ph;
-  const float inv_rho = 1.0f / rho;
+  const float inv_rho = __frcp_rn(rho);
   const float gr0 = P.drho * g0, gr1 = P.drho * g1, gr2 = P.drho * g2;
   const float nu = (P.mu_g + P.dmu * ph) * inv_rho;
-  const float omega = 1.0f / (0.5f + 3.0f * nu);
+  const float omega = __frcp_rn(0.5f + 3.0f * nu);
 
   // capillary force, Eq. 19
   const float muphi = P.beta4 * ph * (ph - 1.0f) * (ph - 0.5f) - P.kap * lap;
@@ -97,27 +125,29 @@ k_hydro(const KParams P, const typename Store<S>::T *__restrict__ src, typename 
     F0 += fr.x; F1 += fr.y; F2 += fr.z;
   }
 
-  // moments, Eqs. 6-7
-  float ps = 0.f, j0 = 0.f, j1 = 0.f, j2 = 0.f;
+  // moments, Eqs. 6-7, pairwise: s = f_i + f_-i, d = f_i - f_-i
+  float ps = f[0], j0 = 0.f, j1 = 0.f, j2 = 0.f;
   float m00 = 0.f, m11 = 0.f, m22 = 0.f, m01 = 0.f, m02 = 0.f, m12 = 0.f;
 #pragma unroll
-  for (int i = 0; i < L::Q; i++) {
-    const float fi = f[i];
-    ps += fi;
+  for (int i = 1; i < L::Q; i++) {
+    if (!(i > L::opp(i))) continue;
+    const float sp = f[i] + f[L::opp(i)], dm = f[i] - f[L::opp(i)];
+    ps += sp;
     const int c0 = L::c(i, 0), c1 = L::c(i, 1), c2 = L::c(i, 2);
-    if (c0) { j0 += c0 * fi; m00 += fi; }
-    if (c1) { j1 += c1 * fi; m11 += fi; }
-    if (c2) { j2 += c2 * fi; m22 += fi; }
-    if (c0 && c1) m01 += c0 * c1 * fi;
-    if (c0 && c2) m02 += c0 * c2 * fi;
-    if (c1 && c2) m12 += c1 * c2 * fi;
+    if (c0) { j0 += c0 * dm; m00 += sp; }
+    if (c1) { j1 += c1 * dm; m11 += sp; }
+    if (c2) { j2 += c2 * dm; m22 += sp; }
+    if (c0 && c1) m01 += c0 * c1 * sp;
+    if (c0 && c2) m02 += c0 * c2 * sp;
+    if (c1 && c2) m12 += c1 * c2 * sp;
   }
 
   // pressure correction (Eq. 20) and buoyancy
   const float pc = -ps * kCs2;
-  F0 += pc * gr0 + (rho - P.rho_bar) * P.g[0];
-  F1 += pc * gr1 + (rho - P.rho_bar) * P.g[1];
-  F2 += pc * gr2 + (rho - P.rho_bar) * P.g[2];
+  const float db = rho - P.rho_bar;
+  F0 += pc * gr0 + db * P.g[0];
+  F1 += pc * gr1 + db * P.g[1];
+  F2 += pc * gr2 + db * P.g[2];
 
   // velocity without F_nu, then the viscous correction (Eq. 21) from Pi = M2 - p* cs^2 I - u0 u0
   const float h2r = 0.5f * inv_rho;
@@ -156,23 +186,24 @@ k_hydro(const KParams P, const typename Store<S>::T *__restrict__ src, typename 
   const float uu = u0 * u0 + u1 * u1 + u2 * u2;
   const float ur = u0 * r0 + u1 * r1 + u2 * r2;
   const float om1 = 1.0f - omega;
+  const float C0 = ps - 1.5f * uu - 1.5f * om1 * trA - 1.5f * ur;
+  const float C1 = 3.0f - 4.5f * uu - 4.5f * om1 * trA;
+  const float k45 = 4.5f * om1, k135 = 13.5f * om1, k9 = 9.0f * om1;
 
+  Store<S>::st_w(dst + idx, C0, L::w(0));
 #pragma unroll
-  for (int i = 0; i < L::Q; i++) {
+  for (int i = 1; i < L::Q; i++) {
+    if (!(i > L::opp(i))) continue;
     const int c0 = L::c(i, 0), c1 = L::c(i, 1), c2 = L::c(i, 2);
     const float cu = c0 * u0 + c1 * u1 + c2 * u2;
     const float cr = c0 * r0 + c1 * r1 + c2 * r2;
     const float cAc = c0 * c0 * A00 + c1 * c1 * A11 + c2 * c2 * A22 +
                       2.0f * (c0 * c1 * A01 + c0 * c2 * A02 + c1 * c2 * A12);
     const float cAu = c0 * Au0 + c1 * Au1 + c2 * Au2;
-    // Eq. 11 (1/(2 cs^4) = 1/(6 cs^6) = 4.5; 3 cs^2 = 1)
-    const float feq = ps + 3.0f * cu + 4.5f * (cu * cu - kCs2 * uu) + 4.5f * (cu * cu * cu - uu * cu);
-    // Eq. 14 with A3 of Eq. 16
-    const float reg = 4.5f * (cAc - kCs2 * trA) + 4.5f * (3.0f * cu * cAc - cu * trA - 2.0f * cAu);
-    // Eq. 17 (1/cs^2 = 3, 1/cs^4 = 9)
-    const float src_i = 3.0f * (cr - ur) + 9.0f * cu * cr;
-    const float fpost = L::w(i) * (feq + om1 * reg + 0.5f * src_i);
-    Store<S>::st(dst + (long long)i * N + idx, fpost, L::w(i));
+    const float ev = C0 + cu * (4.5f * cu + 4.5f * cr) + k45 * cAc;
+    const float od = cu * (C1 + 4.5f * cu * cu + k135 * cAc) - k9 * cAu + 1.5f * cr;
+    Store<S>::st_w(dst + (long long)i * N + idx, ev + od, L::w(i));
+    Store<S>::st_w(dst + (long long)L::opp(i) * N + idx, ev - od, L::w(i));
   }
   u_out[idx] = u0;
   u_out[N + idx] = u1;
@@ -181,25 +212,26 @@ k_hydro(const KParams P, const typename Store<S>::T *__restrict__ src, typename 
 
 template <class L, int S>
 cudaError_t launch_hydro_t(int mode, const KParams &P, const void *src, void *dst, const int32_t *phi,
-                           const float4 *frep, float *u, float *pstar, cudaStream_t s) {
+                           const float4 *frep, float *u, float *pstar, int *reset, cudaStream_t s) {
   using TT = Tile<L::D>;
   using T = typename Store<S>::T;
   dim3 block(TT::X, TT::Y, TT::Z);
   dim3 grid((P.nx + TT::X - 1) / TT::X, (P.ny + TT::Y - 1) / TT::Y, (P.nz + TT::Z - 1) / TT::Z);
   if (mode == kStep)
-    k_hydro<L, S, kStep><<<grid, block, 0, s>>>(P, (const T *)src, (T *)dst, phi, frep, u, pstar);
+    k_hydro<L, S, kStep><<<grid, block, 0, s>>>(P, (const T *)src, (T *)dst, phi, frep, u, pstar, reset);
   else
-    k_hydro<L, S, kMoments><<<grid, block, 0, s>>>(P, (const T *)src, (T *)dst, phi, frep, u, pstar);
+    k_hydro<L, S, kMoments><<<grid, block, 0, s>>>(P, (const T *)src, (T *)dst, phi, frep, u, pstar, reset);
   return cudaGetLastError();
 }
 
 template <class L>
 cudaError_t launch_hydro_lattice(int store, int mode, const KParams &P, const void *src, void *dst,
-                                 const int32_t *phi, const float4 *frep, float *u, float *pstar, cudaStream_t s) {
+                                 const int32_t *phi, const float4 *frep, float *u, float *pstar, int *reset,
+                                 cudaStream_t s) {
   switch (store) {
-    case 0: return launch_hydro_t<L, 0>(mode, P, src, dst, phi, frep, u, pstar, s);
-    case 1: return launch_hydro_t<L, 1>(mode, P, src, dst, phi, frep, u, pstar, s);
-    default: return launch_hydro_t<L, 2>(mode, P, src, dst, phi, frep, u, pstar, s);
+    case 0: return launch_hydro_t<L, 0>(mode, P, src, dst, phi, frep, u, pstar, reset, s);
+    case 1: return launch_hydro_t<L, 1>(mode, P, src, dst, phi, frep, u, pstar, reset, s);
+    default: return launch_hydro_t<L, 2>(mode, P, src, dst, phi, frep, u, pstar, reset, s);
   }
 }
 

@@ -5,19 +5,27 @@
 namespace lbm {
 
 cudaError_t launch_hydro_q9(int, int, const KParams &, const void *, void *, const int32_t *, const float4 *,
-                            float *, float *, cudaStream_t);
+                            float *, float *, int *, cudaStream_t);
 cudaError_t launch_hydro_q19(int, int, const KParams &, const void *, void *, const int32_t *, const float4 *,
-                             float *, float *, cudaStream_t);
+                             float *, float *, int *, cudaStream_t);
 cudaError_t launch_hydro_q27(int, int, const KParams &, const void *, void *, const int32_t *, const float4 *,
-                             float *, float *, cudaStream_t);
+                             float *, float *, int *, cudaStream_t);
 
 cudaError_t launch_hydro(int Q, int store, int mode, const KParams &P, const void *src, void *dst,
-                         const int32_t *phi, const float4 *frep, float *u, float *pstar, cudaStream_t s) {
+                         const int32_t *phi, const float4 *frep, float *u, float *pstar, int *reset,
+                         cudaStream_t s) {
   switch (Q) {
-    case 9: return launch_hydro_q9(store, mode, P, src, dst, phi, frep, u, pstar, s);
-    case 19: return launch_hydro_q19(store, mode, P, src, dst, phi, frep, u, pstar, s);
-    default: return launch_hydro_q27(store, mode, P, src, dst, phi, frep, u, pstar, s);
+    case 9: return launch_hydro_q9(store, mode, P, src, dst, phi, frep, u, pstar, reset, s);
+    case 19: return launch_hydro_q19(store, mode, P, src, dst, phi, frep, u, pstar, reset, s);
+    default: return launch_hydro_q27(store, mode, P, src, dst, phi, frep, u, pstar, reset, s);
   }
+}
+
+int tile_count(int dim, const KParams &P) {
+  using T2 = PhaseTile<2>;
+  using T3 = PhaseTile<3>;
+  if (dim == 2) return ((P.nx + T2::X - 1) / T2::X) * ((P.ny + T2::Y - 1) / T2::Y);
+  return ((P.nx + T3::X - 1) / T3::X) * ((P.ny + T3::Y - 1) / T3::Y) * ((P.nz + T3::Z - 1) / T3::Z);
 }
 
 static inline dim3 grid1d(long long n, int bs) {

@@ -14,16 +14,24 @@ struct NciTable {
 // Kernel modes of the hydrodynamic kernel.
 enum HydroMode { kStep = 0, kMoments = 1 };
 
+// tiles == nullptr: every tile (debug = 1 also writes zero force / no partner at every cell);
+// otherwise only the ntiles listed tiles, walked by list_blocks resident blocks.
 cudaError_t launch_nci(int dim, const KParams &P, const NciTable &T, const int32_t *phi, float4 *frep,
-                       int32_t *partner, int debug, cudaStream_t s);
+                       int32_t *partner, int debug, const int *tiles, const int *ntiles, int list_blocks,
+                       cudaStream_t s);
+int nci_list_blocks(int dim);
 
 // src/dst are population buffers of the store type; MODE kStep writes dst and u, kMoments writes
 // u and pstar only.
 cudaError_t launch_hydro(int Q, int store, int mode, const KParams &P, const void *src, void *dst,
-                         const int32_t *phi, const float4 *frep, float *u, float *pstar, cudaStream_t s);
-
-cudaError_t launch_phase(int dim, const KParams &P, const int32_t *phi, const float *u, int32_t *phi_out,
+                         const int32_t *phi, const float4 *frep, float *u, float *pstar, int *reset,
                          cudaStream_t s);
+
+// Also appends to tiles/ntiles (if not null) the tiles of phi_out that hold an interfacial cell.
+cudaError_t launch_phase(int dim, const KParams &P, const int32_t *phi, const float *u, int32_t *phi_out,
+                         int *tiles, int *ntiles, cudaStream_t s);
+cudaError_t launch_gate_tiles(int dim, const KParams &P, const int32_t *phi, int *tiles, int *ntiles, cudaStream_t s);
+int tile_count(int dim, const KParams &P);
 
 // Conversions between host-layout FP64 staging buffers and the device state.
 cudaError_t launch_phi_in(const KParams &P, const double *phi64, int32_t *phi, cudaStream_t s);

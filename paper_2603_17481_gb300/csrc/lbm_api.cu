@@ -8,6 +8,7 @@
 //   frep     N float4     near-contact force, valid at gated cells only
 //   mom      4*N float    u and p* of lbm_read_fields / lbm_mass (allocated on first use)
 //   stage    k*N double   FP64 staging of host I/O (allocated on first use, grown as needed)
+//   tiles[2] int          near-contact tiles holding an interfacial cell of phi[k] (+ 2 counts)
 //   red      reduction partials and result
 #include <algorithm>
 #include <climits>
@@ -43,6 +44,9 @@ struct lbm_ctx {
   double *stage = nullptr;
   size_t stage_bytes = 0;
   int32_t *partner = nullptr;
+  int *tiles[2] = {nullptr, nullptr};
+  int *ntiles = nullptr;  // 2 counters, one per phi buffer
+  int nci_blocks = 0;
   ReduceOut *red_part = nullptr, *red_out = nullptr;
   int cur = 0;        // population buffer holding the current state
   int pcur = 0;       // phi buffer holding phi^n
@@ -190,9 +194,14 @@ int d2h(lbm_ctx *c, void *dst, const void *src, size_t bytes) {
 }
 int sync(lbm_ctx *c) { return from_cuda(cudaStreamSynchronize(c->stream)); }
 
-// rho_bar from the exact phi sum; also records the phi-mass reference of the conservation check.
+// rho_bar from the exact phi sum; also records the phi-mass reference of the conservation check
+// and lists the near-contact tiles of the initial phi.
 int finish_init(lbm_ctx *c) {
-  int rc = from_cuda(launch_reduce(c->K, c->phi[c->pcur], c->u, c->red_part, c->red_out, c->stream));
+  int rc = from_cuda(cudaMemsetAsync(c->ntiles, 0, 2 * sizeof(int), c->stream));
+  if (rc) return rc;
+  rc = from_cuda(launch_gate_tiles(c->P.dim, c->K, c->phi[c->pcur], c->tiles[c->pcur], c->ntiles + c->pcur, c->stream));
+  if (rc) return rc;
+  rc = from_cuda(launch_reduce(c->K, c->phi[c->pcur], c->u, c->red_part, c->red_out, c->stream));
   if (rc) return rc;
   ReduceOut r;
   if ((rc = d2h(c, &r, c->red_out, sizeof(r)))) return rc;
@@ -212,13 +221,14 @@ int run_moments(lbm_ctx *c) {
   const int d = c->P.dim;
   if (c->P.nci_on) {
     rc = from_cuda(timed(c, LBM_K_NCI, [&] {
-      return launch_nci(d, c->K, c->T, c->phi[c->pcur], c->frep, nullptr, 0, c->stream);
+      return launch_nci(d, c->K, c->T, c->phi[c->pcur], c->frep, nullptr, 0, c->tiles[c->pcur],
+                        c->ntiles + c->pcur, c->nci_blocks, c->stream);
     }));
     if (rc) return rc;
   }
   return from_cuda(timed(c, LBM_K_HYDRO, [&] {
     return launch_hydro(c->P.Q, c->P.store, kMoments, c->K, c->pop[c->cur], nullptr, c->phi[c->pcur], c->frep,
-                        c->mom, c->mom + 3 * c->N, c->stream);
+                        c->mom, c->mom + 3 * c->N, nullptr, c->stream);
   }));
 }
 
@@ -255,6 +265,15 @@ int lbm_create(const lbm_params *p, lbm_ctx **out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->phi[1], sizeof(int32_t) * c->N);
   if (e == cudaSuccess) e = cudaMalloc(&c->u, sizeof(float) * 3 * c->N);
   if (e == cudaSuccess) e = cudaMalloc(&c->frep, sizeof(float4) * c->N);
+  const int ntile = tile_count(p->dim, c->K);
+  if (e == cudaSuccess) e = cudaMalloc(&c->tiles[0], sizeof(int) * ntile);
+  if (e == cudaSuccess) e = cudaMalloc(&c->tiles[1], sizeof(int) * ntile);
+  if (e == cudaSuccess) e = cudaMalloc(&c->ntiles, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->ntiles, 0, 2 * sizeof(int));
+  if (e == cudaSuccess) {
+    c->nci_blocks = nci_list_blocks(p->dim);
+    if (c->nci_blocks <= 0) e = cudaErrorInvalidConfiguration;
+  }
   if (e == cudaSuccess) e = cudaMalloc(&c->red_part, sizeof(ReduceOut) * kReduceBlocks);
   if (e == cudaSuccess) e = cudaMalloc(&c->red_out, sizeof(ReduceOut));
   if (e == cudaSuccess) e = cudaMemset(c->u, 0, sizeof(float) * 3 * c->N);
@@ -281,6 +300,7 @@ void lbm_destroy(lbm_ctx *c) {
   cudaFree(c->phi[0]); cudaFree(c->phi[1]);
   cudaFree(c->u); cudaFree(c->frep); cudaFree(c->mom); cudaFree(c->stage);
   cudaFree(c->partner); cudaFree(c->red_part); cudaFree(c->red_out);
+  cudaFree(c->tiles[0]); cudaFree(c->tiles[1]); cudaFree(c->ntiles);
   delete c;
 }
 
@@ -356,18 +376,25 @@ int lbm_step(lbm_ctx *c, int n) {
   for (int s = 0; s < n; s++) {
     const int nxt = c->cur ^ 1, pn = c->pcur ^ 1;
     int rc;
-    if (c->P.nci_on) {
+    // near-contact pass over the tiles listed for phi^n; the hydrodynamic pass then clears that
+    // list's count, and the phase-field pass lists the tiles of phi^{n+1}
+    const bool nci = c->P.nci_on != 0;
+    if (nci) {
       rc = from_cuda(timed(c, LBM_K_NCI, [&] {
-        return launch_nci(d, c->K, c->T, c->phi[c->pcur], c->frep, nullptr, 0, c->stream);
+        return launch_nci(d, c->K, c->T, c->phi[c->pcur], c->frep, nullptr, 0, c->tiles[c->pcur],
+                          c->ntiles + c->pcur, c->nci_blocks, c->stream);
       }));
       if (rc) return rc;
     }
     rc = from_cuda(timed(c, LBM_K_HYDRO, [&] {
       return launch_hydro(c->P.Q, c->P.store, kStep, c->K, c->pop[c->cur], c->pop[nxt], c->phi[c->pcur], c->frep,
-                          c->u, nullptr, c->stream);
+                          c->u, nullptr, nci ? c->ntiles + c->pcur : nullptr, c->stream);
     }));
     if (rc) return rc;
-    rc = from_cuda(timed(c, LBM_K_PHASE, [&] { return launch_phase(d, c->K, c->phi[c->pcur], c->u, c->phi[pn], c->stream); }));
+    rc = from_cuda(timed(c, LBM_K_PHASE, [&] {
+      return launch_phase(d, c->K, c->phi[c->pcur], c->u, c->phi[pn], nci ? c->tiles[pn] : nullptr,
+                          nci ? c->ntiles + pn : nullptr, c->stream);
+    }));
     if (rc) return rc;
     c->cur = nxt;
     c->pcur = pn;
@@ -447,7 +474,7 @@ int lbm_read_nci(lbm_ctx *c, int32_t *partner, double *frep) {
   }
   if ((rc = ensure_stage(c, sizeof(double) * 3 * N))) return rc;
   rc = from_cuda(timed(c, LBM_K_NCI, [&] {
-    return launch_nci(c->P.dim, c->K, c->T, c->phi[c->pcur], c->frep, c->partner, 1, c->stream);
+    return launch_nci(c->P.dim, c->K, c->T, c->phi[c->pcur], c->frep, c->partner, 1, nullptr, nullptr, 0, c->stream);
   }));
   if (rc) return rc;
   if (partner && (rc = d2h(c, partner, c->partner, sizeof(int32_t) * 3 * N))) return rc;

@@ -28,6 +28,8 @@ struct D2Q9 {
     return i == 0 ? 4.0f / 9.0f : (i < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
   }
   __host__ __device__ static constexpr double wd(int i) { return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0); }
+  // index of -c_i: within each |c|^2 class the order is reversed by negation
+  __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : (i < 5 ? 5 - i : 13 - i); }
 };
 
 struct D3Q19 {
@@ -43,6 +45,7 @@ struct D3Q19 {
     return i == 0 ? 1.0f / 3.0f : (i < 7 ? 1.0f / 18.0f : 1.0f / 36.0f);
   }
   __host__ __device__ static constexpr double wd(int i) { return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0); }
+  __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : (i < 7 ? 7 - i : 25 - i); }
 };
 
 struct D3Q27 {
@@ -61,6 +64,9 @@ struct D3Q27 {
   }
   __host__ __device__ static constexpr double wd(int i) {
     return i == 0 ? 8.0 / 27.0 : (i < 7 ? 2.0 / 27.0 : (i < 19 ? 1.0 / 54.0 : 1.0 / 216.0));
+  }
+  __host__ __device__ static constexpr int opp(int i) {
+    return i == 0 ? 0 : (i < 7 ? 7 - i : (i < 19 ? 25 - i : 45 - i));
   }
 };
 
@@ -84,16 +90,20 @@ template <> struct Store<0> {
   using T = float;
   __device__ static __forceinline__ float ld(const T *p, float) { return __ldg(p); }
   __device__ static __forceinline__ void st(T *p, float v, float) { *p = v; }
+  // stores f given f / w
+  __device__ static __forceinline__ void st_w(T *p, float v_over_w, float w) { *p = w * v_over_w; }
 };
 template <> struct Store<1> {
   using T = __half;
   __device__ static __forceinline__ float ld(const T *p, float w) { return __half2float(__ldg(p)) * w; }
   __device__ static __forceinline__ void st(T *p, float v, float w) { *p = __float2half_rn(v / w); }
+  __device__ static __forceinline__ void st_w(T *p, float v_over_w, float) { *p = __float2half_rn(v_over_w); }
 };
 template <> struct Store<2> {
   using T = __nv_bfloat16;
   __device__ static __forceinline__ float ld(const T *p, float w) { return __bfloat162float(__ldg(p)) * w; }
   __device__ static __forceinline__ void st(T *p, float v, float w) { *p = __float2bfloat16_rn(v / w); }
+  __device__ static __forceinline__ void st_w(T *p, float v_over_w, float) { *p = __float2bfloat16_rn(v_over_w); }
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -121,6 +131,8 @@ __host__ __device__ __forceinline__ int wrapi(int a, int n) {
   a %= n;
   return a < 0 ? a + n : a;
 }
+// Periodic wrap with a fast path for in-range coordinates.
+__device__ __forceinline__ int wrapn(int a, int n) { return (unsigned)a < (unsigned)n ? a : wrapi(a, n); }
 
 // ---------------------------------------------------------------------------------------------
 // Kernel parameter block (derived on the host in FP64, stored as FP32).
@@ -155,8 +167,7 @@ template <int DIM> struct NciTile;
 template <> struct NciTile<2> { static constexpr int X = 32, Y = 16, Z = 1; };
 template <> struct NciTile<3> { static constexpr int X = 32, Y = 4, Z = 4; };
 
-template <int DIM> struct PhaseTile;
-template <> struct PhaseTile<2> { static constexpr int X = 32, Y = 8, Z = 1; };
-template <> struct PhaseTile<3> { static constexpr int X = 32, Y = 4, Z = 2; };
+// The phase-field kernel lists near-contact tiles, so both use the same tiling.
+template <int DIM> struct PhaseTile : NciTile<DIM> {};
 
 }  // namespace lbm
