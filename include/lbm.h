@@ -121,6 +121,22 @@ int lbm_read_fields(lbm_ctx *ctx, double *phi, double *u, double *pstar);
  * sum(rho u) (3 values, u as in lbm_read_fields). Either pointer may be NULL. */
 int lbm_mass(lbm_ctx *ctx, double *phi_mass, double *mom);
 
+/* The same integrals as lbm_mass without allocating any device memory, for callers that cannot
+ * allocate at that moment: a process whose device memory is reserved by another allocator (a
+ * framework's caching allocator owning nearly all of HBM), or a latency-critical loop that cannot
+ * take cudaMalloc's implicit device synchronisation. The paper has no counterpart; it is a service
+ * of this library. The reduction scratch is a fixed static device array (4097 slots of 40 bytes,
+ * about 160 KB) that every GPU loading the library holds until the process exits.
+ * Limits and errors: at most 16,777,216 cells (one slot per 4096 cells), else LBM_ERR_ARG; the
+ * context's device must be current, else LBM_ERR_ARG; the moment buffer must already exist, i.e.
+ * lbm_mass or lbm_read_fields ran once on this context, else LBM_ERR_STATE (it is not allocated
+ * here). The first call on a device looks the scratch address up (cudaGetSymbolAddress); make that
+ * first call during set-up, before any stream capture. All calls on a device share the scratch:
+ * calls whose work overlaps on the GPU (e.g. two contexts on different streams) race, so serialise
+ * them. Each call overwrites every slot it reads; nothing needs clearing between calls.
+ * Synchronises the context stream. Either output pointer may be NULL. */
+int lbm_mass_noalloc(lbm_ctx *ctx, double *phi_mass, double *mom);
+
 /* Near-contact diagnostics on the current phi: partner offsets (3 int32 per cell, INT32_MIN where
  * chi = 0) and the repulsive force density F_rep (3N). Either pointer may be NULL. */
 int lbm_read_nci(lbm_ctx *ctx, int32_t *partner, double *frep);

@@ -71,6 +71,7 @@ def load():
     L.lbm_read_fields.argtypes = [_VP, _VP, _VP, _VP]
     L.lbm_mass.argtypes = [_VP, _VP, _VP]
     L.lbm_read_nci.argtypes = [_VP, _VP, _VP]
+    L.lbm_mass_noalloc.argtypes = [_VP, _VP, _VP]
     L.lbm_synchronize.argtypes = [_VP]
     L.lbm_profile.argtypes = [_VP, ctypes.c_int]
     L.lbm_profile_read.argtypes = [_VP, _VP, _VP]
@@ -80,7 +81,7 @@ def load():
     L.lbm_kernel_name.argtypes = [ctypes.c_int]
     L.lbm_kernel_name.restype = ctypes.c_char_p
     for name in ("lbm_create", "lbm_set_stream", "lbm_init_fields", "lbm_set_state", "lbm_get_state",
-                 "lbm_step", "lbm_read_fields", "lbm_mass", "lbm_read_nci", "lbm_synchronize",
+                 "lbm_step", "lbm_read_fields", "lbm_mass", "lbm_mass_noalloc", "lbm_read_nci", "lbm_synchronize",
                  "lbm_profile", "lbm_profile_read", "lbm_lattice"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -200,6 +201,14 @@ def lbm_mass(ctx: int):
     return m.value, np.array(list(mom))
 
 
+def lbm_mass_noalloc(ctx: int):
+    """lbm_mass without device allocation (static scratch; see include/lbm.h for its limits)."""
+    m = ctypes.c_double()
+    mom = (ctypes.c_double * 3)()
+    _check(load().lbm_mass_noalloc(_VP(ctx), ctypes.addressof(m), ctypes.addressof(mom)), "lbm_mass_noalloc")
+    return m.value, np.array(list(mom))
+
+
 def lbm_read_nci(ctx: int, N: int):
     part = np.empty((N, 3), dtype=np.int32)
     frep = np.empty((3, N))
@@ -272,6 +281,9 @@ class Lbm:
 
     def mass(self):
         return lbm_mass(self.ctx)
+
+    def mass_noalloc(self):
+        return lbm_mass_noalloc(self.ctx)
 
     def read_nci(self):
         return lbm_read_nci(self.ctx, self.N)

@@ -1,0 +1,46 @@
+// ctx.h -- the context behind the opaque lbm_ctx handle of include/lbm.h (internal to the library).
+#pragma once
+
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "launch.h"
+
+struct ProfPair {
+  int kind;
+  cudaEvent_t a, b;
+};
+
+struct lbm_ctx {
+  lbm_params P;
+  lbm::KParams K;
+  lbm::NciTable T;
+  long long N;
+  size_t pop_bytes;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  void *pop[2] = {nullptr, nullptr};
+  int32_t *phi[2] = {nullptr, nullptr};
+  float *u = nullptr;
+  float4 *frep = nullptr;
+  float *mom = nullptr;
+  double *stage = nullptr;
+  size_t stage_bytes = 0;
+  int32_t *partner = nullptr;
+  int *tiles[2] = {nullptr, nullptr};
+  int *ntiles = nullptr;  // 2 counters, one per phi buffer
+  int nci_blocks = 0;
+  lbm::ReduceOut *red_part = nullptr, *red_out = nullptr;
+  int cur = 0;        // population buffer holding the current state
+  int pcur = 0;       // phi buffer holding phi^n
+  bool initialised = false;
+  long long steps = 0;
+  long long phi_q30_ref = 0;
+  // profiler
+  bool prof = false;
+  std::vector<ProfPair> pairs;
+  std::vector<cudaEvent_t> pool;
+  double prof_ms[LBM_K_COUNT] = {0};
+  int64_t prof_n[LBM_K_COUNT] = {0};
+};
+

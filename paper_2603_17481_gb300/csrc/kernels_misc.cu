@@ -239,6 +239,13 @@ __global__ void k_reduce_final(const ReduceOut *__restrict__ partials, int n, Re
   *out = r;
 }
 
+cudaError_t launch_reduce_n(const KParams &P, const int32_t *phi, const float *u, ReduceOut *partials, int nblocks,
+                            ReduceOut *out, cudaStream_t s) {
+  k_reduce_partial<<<nblocks, kReduceThreads, 0, s>>>(P, phi, u, partials);
+  k_reduce_final<<<1, 32, 0, s>>>(partials, nblocks, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reduce(const KParams &P, const int32_t *phi, const float *u, ReduceOut *partials, ReduceOut *out,
                           cudaStream_t s) {
   k_reduce_partial<<<kReduceBlocks, kReduceThreads, 0, s>>>(P, phi, u, partials);

@@ -53,5 +53,8 @@ struct ReduceOut {
 constexpr int kReduceBlocks = 608;  // 4 per SM of a 152-SM GB300
 cudaError_t launch_reduce(const KParams &P, const int32_t *phi, const float *u, ReduceOut *partials,
                           ReduceOut *out, cudaStream_t s);
+// The same reduction on a grid of nblocks blocks (nblocks partial slots).
+cudaError_t launch_reduce_n(const KParams &P, const int32_t *phi, const float *u, ReduceOut *partials,
+                            int nblocks, ReduceOut *out, cudaStream_t s);
 
 }  // namespace lbm

@@ -1,0 +1,58 @@
+"""lbm_mass_noalloc: the integrals of lbm_mass without allocating device memory.
+
+It serves callers that cannot allocate device memory at the moment they need the integrals: a
+process whose HBM is already reserved by another allocator (for instance a framework's caching
+allocator), or a latency-critical loop that cannot take cudaMalloc's implicit synchronisation. Its
+reduction scratch is a static device array, so its results must equal lbm_mass's on the same
+state, call after call. This file is named to be collected last.
+"""
+import numpy as np
+import pytest
+
+from paper_2603_17481_gb300 import binding as B
+from paper_2603_17481_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2603_17481_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def test_noalloc_matches_lbm_mass_on_two_calls_in_a_row():
+    cfg = W.base_config(3, 48, 40, 32, 19, rho_g=0.1)
+    phi, u = W.droplet_fields(cfg, [(16.5, 19.5, 15.5), (31.5, 20.0, 15.5)], [6.0, 6.0],
+                              [(0.02, 0, 0), (-0.02, 0, 0)])
+    sim = B.Lbm(cfg)
+    sim.init_fields(W.to_q30_grid(phi), u)
+    sim.step(7)
+    m_ref, mom_ref = sim.mass()  # lbm_mass also creates the moment buffer the variant reuses
+    for _ in range(2):
+        m, mom = sim.mass_noalloc()
+        assert abs(m - m_ref) <= 1e-12 * abs(m_ref)
+        assert np.max(np.abs(mom - mom_ref)) <= 1e-9
+    sim.step(3)
+    m_ref, mom_ref = sim.mass()
+    m, mom = sim.mass_noalloc()
+    assert abs(m - m_ref) <= 1e-12 * abs(m_ref)
+    assert np.max(np.abs(mom - mom_ref)) <= 1e-9
+
+
+def test_noalloc_refuses_what_it_cannot_do_without_allocating():
+    cfg = W.base_config(3, 24, 16, 16, 19)
+    sim = B.Lbm(cfg)
+    phi, u = W.droplet_fields(cfg, [(12, 8, 8)], [4.0], [(0, 0, 0)])
+    sim.init_fields(phi, u)
+    with pytest.raises(B.LbmError) as ei:  # no moment buffer yet
+        sim.mass_noalloc()
+    assert ei.value.code == B.LBM_ERR_STATE
+    big = B.Lbm(W.base_config(2, 4100, 4100, 1, 9))  # 16,810,000 cells: beyond the 16,777,216 limit
+    with pytest.raises(B.LbmError) as ei:
+        big.mass_noalloc()
+    assert ei.value.code == B.LBM_ERR_ARG
+    big.close()
