@@ -23,6 +23,7 @@ struct lbm_ctx {
   int32_t *phi[2] = {nullptr, nullptr};
   float *u = nullptr;
   float4 *frep = nullptr;
+  float4 *nrm = nullptr;  // interface normals at gated cells
   float *mom = nullptr;
   double *stage = nullptr;
   size_t stage_bytes = 0;

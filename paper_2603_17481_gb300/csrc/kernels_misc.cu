@@ -228,15 +228,28 @@ k_reduce_partial(const KParams P, const int32_t *__restrict__ phi, const float *
   }
 }
 
+// One warp: lane l sums partials l, l + 32, ... in order, then a fixed shuffle tree.
 __global__ void k_reduce_final(const ReduceOut *__restrict__ partials, int n, ReduceOut *__restrict__ out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  ReduceOut r{0, {0.0, 0.0, 0.0}, 0};
-  for (int k = 0; k < n; k++) {
-    r.phi_q30 += partials[k].phi_q30;
-    r.nonfinite += partials[k].nonfinite;
-    for (int a = 0; a < 3; a++) r.mom[a] += partials[k].mom[a];
+  if (blockIdx.x != 0) return;
+  const int lane = threadIdx.x;
+  long long sphi = 0, nonfin = 0;
+  double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+  for (int k = lane; k < n; k += 32) {
+    sphi += partials[k].phi_q30;
+    nonfin += partials[k].nonfinite;
+    m0 += partials[k].mom[0];
+    m1 += partials[k].mom[1];
+    m2 += partials[k].mom[2];
   }
-  *out = r;
+  m0 = warp_sum(m0); m1 = warp_sum(m1); m2 = warp_sum(m2);
+  sphi = warp_sum_ll(sphi); nonfin = warp_sum_ll(nonfin);
+  if (lane == 0) {
+    ReduceOut r;
+    r.phi_q30 = sphi;
+    r.nonfinite = nonfin;
+    r.mom[0] = m0; r.mom[1] = m1; r.mom[2] = m2;
+    *out = r;
+  }
 }
 
 cudaError_t launch_reduce_n(const KParams &P, const int32_t *phi, const float *u, ReduceOut *partials, int nblocks,

@@ -1,235 +1,280 @@
 // kernels_nci.cu -- near-contact interaction (Sec. 2.3): interfacial gate (Eqs. 58-59), bounded
 // window pairing (Eqs. 60-65), closed-form proximity indicator and repulsive force (Eqs. 66-73).
 //
-// A block handles one tile: its phi plus a halo of 4 cells (window radius <= 3 plus the gradient
-// stencil) is staged in shared memory, normals are computed only at gated cells of the tile + 3
-// halo, and the gated cells of the tile are compacted into a list that the warps share out: one
-// warp per gated cell, 32 window offsets per iteration in (|r|^2, canonical index) order, stopping
-// after the first shell that holds an accepted candidate. Only tiles listed as holding a gated
-// cell are visited in a time step. The force is written only at gated cells; the hydrodynamic
-// kernel reads it exactly there (same gate function).
+// Two passes over the tiles that hold an interfacial (gated) cell, as listed by the phase-field
+// kernel of the previous step (or over every tile for the diagnostic read-back):
+//   k_nci_normals  the normal n = grad(phi) / (|grad(phi)| + eps_n) of every gated cell (Eq. 57,
+//                  isotropic gradient of Eq. 22), computed once and stored as a float4;
+//   k_nci_scan     per tile: phi and the gated normals of the tile + 3 halo staged in shared memory,
+//                  the gated cells of the tile compacted into a list, then one warp per gated cell
+//                  tests 32 window offsets per iteration in (|r|^2, canonical index) order and
+//                  stops after the first shell holding an accepted candidate.
+// Before scanning, each tile bounds n(x).n(y) from below over its whole halo box by the component
+// ranges [lo_a, hi_a] of its gated normals: sum_a min(n_a lo_a, n_a hi_a) <= n(x).n(y). A cell whose
+// bound exceeds the facing threshold cannot have a candidate (Eq. 62) and skips the scan; this is
+// exact (a rounding margin of 1e-5 is kept), and it removes the scan on isolated interfaces.
+// The force is written only at gated cells; the hydrodynamic kernel reads it exactly there (same
+// gate function).
 #include "launch.h"
 
 namespace lbm {
 
 template <int DIM> struct NciGeom {
   static constexpr int TX = NciTile<DIM>::X, TY = NciTile<DIM>::Y, TZ = NciTile<DIM>::Z;
-  static constexpr int H = 4;  // phi halo
+  static constexpr int H = 3;  // window radius bound
   static constexpr int HX = TX + 2 * H, HY = TY + 2 * H, HZ = DIM == 3 ? TZ + 2 * H : 1;
   static constexpr int NB = HX * HY * HZ;
-  static constexpr int GX = TX + 2 * (H - 1), GY = TY + 2 * (H - 1), GZ = DIM == 3 ? TZ + 2 * (H - 1) : 1;
-  static constexpr int NG = GX * GY * GZ;
-  static constexpr int NT = TX * TY * TZ;
-  static constexpr size_t smem = sizeof(int32_t) * NB + sizeof(float) * 3 * NG + sizeof(int) * (NT + 1);
+  static constexpr int NT = TX * TY * TZ, NW = NT / 32;
+  static constexpr size_t smem =
+      sizeof(int32_t) * NB + sizeof(float) * 3 * NB + sizeof(int) * (NT + 1) + sizeof(float) * 6 * (NW + 1);
 };
 
-// One tile of the near-contact pass. All threads of the block call it with the same tile.
 template <int DIM>
-__device__ __forceinline__ void nci_tile(const KParams &P, const NciTable &T, const int32_t *__restrict__ phi,
-                                         float4 *__restrict__ frep, int32_t *__restrict__ partner, int debug,
-                                         int bx, int by, int bz, int32_t *s_phi, float *s_n) {
+__device__ __forceinline__ void tile_of(int tile, int gtx, int gty, int &bx, int &by, int &bz) {
+  bx = tile % gtx;
+  by = (tile / gtx) % gty;
+  bz = tile / (gtx * gty);
+}
+
+// Normals of the gated cells of the listed tiles (or of every tile when tiles == nullptr).
+template <int DIM>
+__global__ void __launch_bounds__(NciGeom<DIM>::NT)
+k_nci_normals(const KParams P, const int32_t *__restrict__ phi, float4 *__restrict__ nrm,
+              const int *__restrict__ tiles, const int *__restrict__ ntiles, int total, int gtx, int gty) {
   using G = NciGeom<DIM>;
   using SL = typename StencilOf<DIM>::type;
-  const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
-  const int tid = tx + G::TX * (ty + G::TY * tz);
-  const int x0 = bx * G::TX, y0 = by * G::TY, z0 = bz * G::TZ;
-  const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
-  const bool inb = x < P.nx && y < P.ny && z < P.nz;
-  const long long idx = inb ? (long long)x + (long long)P.nx * (y + (long long)P.ny * z) : 0;
-
-  const int32_t v = inb ? phi[idx] : 0;
-  const float qx = q_gate_value(v);
-  const bool gated = inb && (qx >= P.q_th);
-  if (!__syncthreads_or(gated) && !debug) return;
-
-  // phi box with periodic wrap, loaded row by row (rows of HX = TX + 8 values)
-  {
-    const int xl = wrapn(x0 - G::H + tx, P.nx);
-    const int xr = wrapn(x0 - G::H + 32 + (tx & 7), P.nx);
-    constexpr int NROWS = G::HY * G::HZ, NW = G::TY * G::TZ;
-    for (int r = ty + G::TY * tz; r < NROWS; r += NW) {
-      const int ry = r % G::HY, rz = r / G::HY;
-      const int Y = wrapn(y0 + ry - G::H, P.ny);
-      const int Z = DIM == 3 ? wrapn(z0 + rz - G::H, P.nz) : 0;
-      const int32_t *row = phi + (long long)P.nx * (Y + (long long)P.ny * Z);
-      s_phi[r * G::HX + tx] = row[xl];
-      if (tx < 8) s_phi[r * G::HX + 32 + tx] = row[xr];
-    }
-  }
-  __syncthreads();
-
-  // normals (Eq. 57, isotropic gradient of Eq. 22) at gated cells of the tile + 3 halo
-  for (int t = tid; t < G::NG; t += G::NT) {
-    int gx = t % G::GX, gy = (t / G::GX) % G::GY, gz = t / (G::GX * G::GY);
-    int b = (DIM == 3 ? (gz + 1) * G::HX * G::HY : 0) + (gy + 1) * G::HX + gx + 1;
-    int32_t vc = s_phi[b];
-    if (q_gate_value(vc) >= P.q_th) {
-      float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+  const int n = tiles ? *ntiles : total;
+  const int nx = P.nx, ny = P.ny, nz = P.nz;
+  for (int t = blockIdx.x; t < n; t += gridDim.x) {
+    int bx, by, bz;
+    tile_of<DIM>(tiles ? tiles[t] : t, gtx, gty, bx, by, bz);
+    const int x = bx * G::TX + threadIdx.x, y = by * G::TY + threadIdx.y, z = bz * G::TZ + threadIdx.z;
+    if (x >= nx || y >= ny || z >= nz) continue;
+    const int X[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
+    const int Y[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
+    int Z[3] = {0, 0, 0};
+    if (DIM == 3) { Z[0] = z == 0 ? nz - 1 : z - 1; Z[1] = z; Z[2] = z == nz - 1 ? 0 : z + 1; }
+    const long long idx = (long long)x + (long long)nx * (y + (long long)ny * z);
+    const int32_t v = phi[idx];
+    if (!(q_gate_value(v) >= P.q_th)) continue;
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
 #pragma unroll
-      for (int i = 1; i < SL::Q; i++) {
-        if (!positive<SL>(i)) continue;
-        const int o = SL::c(i, 0) + G::HX * (SL::c(i, 1) + G::HY * SL::c(i, 2));
-        const float d = SL::w(i) * dphi_of(s_phi[b + o], s_phi[b - o]);
-        g0 += SL::c(i, 0) * d;
-        g1 += SL::c(i, 1) * d;
-        if (DIM == 3) g2 += SL::c(i, 2) * d;
-      }
-      g0 *= 3.0f; g1 *= 3.0f; g2 *= 3.0f;
-      const float inv = 1.0f / (sqrtf(g0 * g0 + g1 * g1 + g2 * g2) + P.eps_n);
-      s_n[t] = g0 * inv;
-      s_n[G::NG + t] = g1 * inv;
-      s_n[2 * G::NG + t] = g2 * inv;
+    for (int i = 1; i < SL::Q; i++) {
+      if (!positive<SL>(i)) continue;
+      const int c0 = SL::c(i, 0), c1 = SL::c(i, 1), c2 = SL::c(i, 2);
+      const long long ip = (long long)X[1 + c0] + (long long)nx * (Y[1 + c1] + (long long)ny * Z[1 + c2]);
+      const long long im = (long long)X[1 - c0] + (long long)nx * (Y[1 - c1] + (long long)ny * Z[1 - c2]);
+      const float d = SL::w(i) * dphi_of(__ldg(phi + ip), __ldg(phi + im));
+      g0 += c0 * d;
+      g1 += c1 * d;
+      if (DIM == 3) g2 += c2 * d;
     }
+    g0 *= 3.0f; g1 *= 3.0f; g2 *= 3.0f;
+    const float inv = 1.0f / (sqrtf(g0 * g0 + g1 * g1 + g2 * g2) + P.eps_n);
+    nrm[idx] = make_float4(g0 * inv, g1 * inv, g2 * inv, 0.0f);
   }
-  // compact list of the tile's gated cells (tile-local linear index)
-  int *s_list = reinterpret_cast<int *>(s_n + 3 * G::NG);
-  int *s_count = s_list + G::NT;
-  if (tid == 0) *s_count = 0;
-  __syncthreads();
-  {
-    const unsigned m = __ballot_sync(0xffffffffu, gated);
-    const int lane = tid & 31;
-    int base = 0;
-    if (lane == 0 && m) base = atomicAdd(s_count, __popc(m));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (gated) s_list[base + __popc(m & ((1u << lane) - 1u))] = tid;
-  }
-  __syncthreads();
+}
 
-  // one warp per gated cell: the 32 lanes test 32 window offsets at a time, in (|r|^2, canonical
-  // index) order; the candidate criteria are Eqs. 59, 61 and 62, and the winner is the nearest
-  // accepted candidate, then the largest facing score, then the first in table order (the
-  // packed key below orders exactly that way).
-  const int lane = tid & 31, warp = tid >> 5;
-  const int ncell = *s_count;
-  for (int k = warp; k < ncell; k += G::NT / 32) {
-    const int c = s_list[k];
-    const int cx = c % G::TX, cy = (c / G::TX) % G::TY, cz = c / (G::TX * G::TY);
-    const int ob = (DIM == 3 ? (cz + G::H) * G::HX * G::HY : 0) + (cy + G::H) * G::HX + cx + G::H;
-    const int on = (DIM == 3 ? (cz + G::H - 1) * G::GX * G::GY : 0) + (cy + G::H - 1) * G::GX + cx + G::H - 1;
-    const int32_t vx = s_phi[ob];
-    const float qxc = q_gate_value(vx);
-    const float n0 = s_n[on], n1 = s_n[G::NG + on], n2 = s_n[2 * G::NG + on];
-    const float sim = __fmul_rn(P.eta, fmaxf(qxc, P.eps_q));
-    unsigned long long best = ~0ull;
-    for (int j0 = 0; j0 < T.count; j0 += 32) {
-      // stop once a candidate is held and this chunk starts beyond its shell
-      if (best != ~0ull && (int)T.o[j0].d2 > (int)(best >> 40)) break;
-      const int j = j0 + lane;
-      unsigned long long key = ~0ull;
-      if (j < T.count) {
-        const NciOffset o = T.o[j];
-        const int32_t vy = s_phi[ob + o.dx + G::HX * (o.dy + G::HY * o.dz)];
-        const float qy = q_gate_value(vy);
-        if (qy >= P.q_th && fabsf(__fsub_rn(qy, qxc)) <= sim) {
-          const int yn = on + o.dx + G::GX * (o.dy + G::GY * o.dz);
-          const float dot = __fadd_rn(__fadd_rn(__fmul_rn(n0, s_n[yn]), __fmul_rn(n1, s_n[G::NG + yn])),
-                                      __fmul_rn(n2, s_n[2 * G::NG + yn]));
-          if (dot <= P.cos_opp) {
-            const float ff = fmaxf(-dot, 0.0f);
-            key = ((unsigned long long)o.d2 << 40) | ((unsigned long long)(0x7fffffffu - __float_as_uint(ff)) << 9) |
-                  (unsigned long long)j;
+template <int DIM>
+__global__ void __launch_bounds__(NciGeom<DIM>::NT)
+k_nci_scan(const KParams P, const NciTable T, const int32_t *__restrict__ phi, const float4 *__restrict__ nrm,
+           float4 *__restrict__ frep, int32_t *__restrict__ partner, int debug, const int *__restrict__ tiles,
+           const int *__restrict__ ntiles, int total, int gtx, int gty) {
+  using G = NciGeom<DIM>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int32_t *s_phi = reinterpret_cast<int32_t *>(smem_raw);
+  float *s_n = reinterpret_cast<float *>(s_phi + G::NB);
+  int *s_list = reinterpret_cast<int *>(s_n + 3 * G::NB);
+  int *s_count = s_list + G::NT;
+  float *s_rng = reinterpret_cast<float *>(s_count + 1);  // [NW + 1][6]
+
+  const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+  const int tid = tx + G::TX * (ty + G::TY * tz), lane = tid & 31, warp = tid >> 5;
+  const int nx = P.nx, ny = P.ny, nz = P.nz;
+  const int n = tiles ? *ntiles : total;
+
+  for (int t = blockIdx.x; t < n; t += gridDim.x) {
+    int bx, by, bz;
+    tile_of<DIM>(tiles ? tiles[t] : t, gtx, gty, bx, by, bz);
+    const int x0 = bx * G::TX, y0 = by * G::TY, z0 = bz * G::TZ;
+    const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
+    const bool inb = x < nx && y < ny && z < nz;
+    const long long idx = inb ? (long long)x + (long long)nx * (y + (long long)ny * z) : 0;
+    const int32_t v = inb ? phi[idx] : 0;
+    const bool gated = inb && (q_gate_value(v) >= P.q_th);
+    if (!__syncthreads_or(gated)) {
+      if (debug && inb) {
+        frep[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (partner) partner[3 * idx] = partner[3 * idx + 1] = partner[3 * idx + 2] = INT32_MIN;
+      }
+      continue;  // uniform over the block
+    }
+
+    // stage phi and the gated normals of the tile + 3 halo (rows of HX = TX + 6 values), and the
+    // component ranges of those normals
+    float lo0 = 1e30f, lo1 = 1e30f, lo2 = 1e30f, hi0 = -1e30f, hi1 = -1e30f, hi2 = -1e30f;
+    {
+      const int xl = wrapn(x0 - G::H + tx, nx);
+      const int xr = wrapn(x0 - G::H + 32 + (tx & 7), nx);
+      constexpr int NROWS = G::HY * G::HZ;
+      for (int r = warp; r < NROWS; r += G::NW) {
+        const int ry = r % G::HY, rz = r / G::HY;
+        const int Yr = wrapn(y0 + ry - G::H, ny);
+        const int Zr = DIM == 3 ? wrapn(z0 + rz - G::H, nz) : 0;
+        const long long row = (long long)nx * (Yr + (long long)ny * Zr);
+#pragma unroll
+        for (int part = 0; part < 2; part++) {
+          if (part == 1 && lane >= G::HX - 32) break;
+          const int col = part == 0 ? lane : 32 + lane;
+          const long long gi = row + (part == 0 ? xl : xr);
+          const int32_t vb = phi[gi];
+          const int b = r * G::HX + col;
+          s_phi[b] = vb;
+          if (q_gate_value(vb) >= P.q_th) {
+            const float4 nb = __ldg(nrm + gi);
+            s_n[b] = nb.x; s_n[G::NB + b] = nb.y; s_n[2 * G::NB + b] = nb.z;
+            lo0 = fminf(lo0, nb.x); lo1 = fminf(lo1, nb.y); lo2 = fminf(lo2, nb.z);
+            hi0 = fmaxf(hi0, nb.x); hi1 = fmaxf(hi1, nb.y); hi2 = fmaxf(hi2, nb.z);
           }
         }
       }
+    }
 #pragma unroll
-      for (int sh = 16; sh > 0; sh >>= 1) {
-        const unsigned long long other = __shfl_xor_sync(0xffffffffu, key, sh);
-        key = other < key ? other : key;
-      }
-      best = key < best ? key : best;
+    for (int sh = 16; sh > 0; sh >>= 1) {
+      lo0 = fminf(lo0, __shfl_xor_sync(0xffffffffu, lo0, sh));
+      lo1 = fminf(lo1, __shfl_xor_sync(0xffffffffu, lo1, sh));
+      lo2 = fminf(lo2, __shfl_xor_sync(0xffffffffu, lo2, sh));
+      hi0 = fmaxf(hi0, __shfl_xor_sync(0xffffffffu, hi0, sh));
+      hi1 = fmaxf(hi1, __shfl_xor_sync(0xffffffffu, hi1, sh));
+      hi2 = fmaxf(hi2, __shfl_xor_sync(0xffffffffu, hi2, sh));
     }
-    if (lane != 0) continue;
-    const long long gidx = (long long)(x0 + cx) + (long long)P.nx * ((y0 + cy) + (long long)P.ny * (z0 + cz));
-    float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (best != ~0ull) {
-      const int bj = (int)(best & 511ull);
-      const NciOffset o = T.o[bj];
-      const float ff = __uint_as_float(0x7fffffffu - (unsigned)((best >> 9) & 0x7fffffffull));
-      const int32_t vy = s_phi[ob + o.dx + G::HX * (o.dy + G::HY * o.dz)];
-      const int yn = on + o.dx + G::GX * (o.dy + G::GY * o.dz);
-      const float m0 = s_n[yn], m1 = s_n[G::NG + yn], m2 = s_n[2 * G::NG + yn];
-      const float qy = q_gate_value(vy);
-      // paired indicator and clamp, Eqs. 66-67
-      const float qpair = 0.5f * (qxc + qy);
-      const float qcl = fminf(fmaxf(qpair, P.eps_q), 0.25f - P.eps_q);
-      // proximity indicator, Eq. 70, as eps * artanh(sqrt(1 - 4 q)): the same value, and
-      // 1 - 4 q_pair = ((1 - 2 phi_x)^2 + (1 - 2 phi_y)^2) / 2 has no cancellation
-      float mm;
-      if (qcl == qpair) {
-        const float ax = 1.0f - 2.0f * fminf(fmaxf(phi_of(vx), 0.f), 1.f);
-        const float ay = 1.0f - 2.0f * fminf(fmaxf(phi_of(vy), 0.f), 1.f);
-        mm = 0.5f * (ax * ax + ay * ay);
-      } else {
-        mm = 1.0f - 4.0f * qcl;
-      }
-      const float h = P.eps * atanhf(sqrtf(mm));
-      const float t = h / P.h0;
-      const float tp = (P.p == 4.0f) ? (t * t) * (t * t) : powf(t, P.p);
-      const float wh = 1.0f / (1.0f + tp);  // Eq. 71
-      // symmetric normal, Eq. 69, line-of-centres fallback, oriented toward the partner
-      const float rn = sqrtf((float)o.d2);
-      const float r0 = o.dx / rn, r1 = o.dy / rn, r2 = o.dz / rn;
-      float s0 = n0 - m0, s1 = n1 - m1, s2 = n2 - m2;
-      const float sn = sqrtf(s0 * s0 + s1 * s1 + s2 * s2);
-      if (sn < 1e-8f) {
-        s0 = r0; s1 = r1; s2 = r2;
-      } else {
-        const float is = 1.0f / (sn + P.eps_n);
-        s0 *= is; s1 *= is; s2 *= is;
-      }
-      if (r0 * s0 + r1 * s1 + r2 * s2 < 0.0f) {
-        s0 = -s0; s1 = -s1; s2 = -s2;
-      }
-      // flux and force density with the facing factor of Eq. 68, Eqs. 72-73
-      const float rho = P.rho_g + P.drho * phi_of(vx);
-      const float amp = rho * P.A_rep * qcl * wh * ff;
-      out = make_float4(amp * s0, amp * s1, DIM == 3 ? amp * s2 : 0.0f, 1.0f);
-      if (partner) {
-        partner[3 * gidx] = o.dx;
-        partner[3 * gidx + 1] = o.dy;
-        partner[3 * gidx + 2] = o.dz;
-      }
-    } else if (partner) {
-      partner[3 * gidx] = partner[3 * gidx + 1] = partner[3 * gidx + 2] = INT32_MIN;
+    if (lane == 0) {
+      float *rw = s_rng + 6 * warp;
+      rw[0] = lo0; rw[1] = lo1; rw[2] = lo2; rw[3] = hi0; rw[4] = hi1; rw[5] = hi2;
     }
-    frep[gidx] = out;
-  }
-  // debug read-back: every non-gated cell reports no partner and zero force
-  if (debug && inb && !gated) {
-    frep[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (partner) partner[3 * idx] = partner[3 * idx + 1] = partner[3 * idx + 2] = INT32_MIN;
-  }
-}
-
-// Every tile of the grid (used for the diagnostic read-back, where every cell reports).
-template <int DIM>
-__global__ void __launch_bounds__(NciGeom<DIM>::NT)
-k_nci_full(const KParams P, const NciTable T, const int32_t *__restrict__ phi, float4 *__restrict__ frep,
-           int32_t *__restrict__ partner, int debug) {
-  using G = NciGeom<DIM>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  int32_t *s_phi = reinterpret_cast<int32_t *>(smem_raw);
-  float *s_n = reinterpret_cast<float *>(smem_raw + sizeof(int32_t) * G::NB);
-  nci_tile<DIM>(P, T, phi, frep, partner, debug, blockIdx.x, blockIdx.y, blockIdx.z, s_phi, s_n);
-}
-
-// Only the tiles listed by the phase-field kernel (those holding an interfacial cell); a grid of
-// resident blocks walks the list.
-template <int DIM>
-__global__ void __launch_bounds__(NciGeom<DIM>::NT)
-k_nci_list(const KParams P, const NciTable T, const int32_t *__restrict__ phi, float4 *__restrict__ frep,
-           const int *__restrict__ tiles, const int *__restrict__ ntiles, int gtx, int gty) {
-  using G = NciGeom<DIM>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  int32_t *s_phi = reinterpret_cast<int32_t *>(smem_raw);
-  float *s_n = reinterpret_cast<float *>(smem_raw + sizeof(int32_t) * G::NB);
-  const int n = *ntiles;
-  for (int t = blockIdx.x; t < n; t += gridDim.x) {
-    const int tile = tiles[t];
-    const int bx = tile % gtx, by = (tile / gtx) % gty, bz = tile / (gtx * gty);
-    nci_tile<DIM>(P, T, phi, frep, nullptr, 0, bx, by, bz, s_phi, s_n);
+    if (tid == 0) *s_count = 0;
     __syncthreads();
+    if (tid < 6) {
+      float a = s_rng[tid];
+      for (int w = 1; w < G::NW; w++) a = tid < 3 ? fminf(a, s_rng[6 * w + tid]) : fmaxf(a, s_rng[6 * w + tid]);
+      s_rng[6 * G::NW + tid] = a;
+    }
+    {  // compact the gated cells of the tile
+      const unsigned m = __ballot_sync(0xffffffffu, gated);
+      int base = 0;
+      if (lane == 0 && m) base = atomicAdd(s_count, __popc(m));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (gated) s_list[base + __popc(m & ((1u << lane) - 1u))] = tid;
+    }
+    if (debug && inb && !gated) {
+      frep[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (partner) partner[3 * idx] = partner[3 * idx + 1] = partner[3 * idx + 2] = INT32_MIN;
+    }
+    __syncthreads();
+    const float rlo0 = s_rng[6 * G::NW], rlo1 = s_rng[6 * G::NW + 1], rlo2 = s_rng[6 * G::NW + 2];
+    const float rhi0 = s_rng[6 * G::NW + 3], rhi1 = s_rng[6 * G::NW + 4], rhi2 = s_rng[6 * G::NW + 5];
+
+    // one warp per gated cell; candidate criteria Eqs. 59, 61, 62; the winner is the nearest
+    // accepted candidate, then the largest facing score, then the first in table order (the
+    // packed key orders exactly that way)
+    const int ncell = *s_count;
+    for (int k = warp; k < ncell; k += G::NW) {
+      const int c = s_list[k];
+      const int cx = c % G::TX, cy = (c / G::TX) % G::TY, cz = c / (G::TX * G::TY);
+      const int ob = (DIM == 3 ? (cz + G::H) * G::HX * G::HY : 0) + (cy + G::H) * G::HX + cx + G::H;
+      const int32_t vx = s_phi[ob];
+      const float qxc = q_gate_value(vx);
+      const float n0 = s_n[ob], n1 = s_n[G::NB + ob], n2 = s_n[2 * G::NB + ob];
+      const float bound = fminf(n0 * rlo0, n0 * rhi0) + fminf(n1 * rlo1, n1 * rhi1) + fminf(n2 * rlo2, n2 * rhi2);
+      unsigned long long best = ~0ull;
+      if (bound <= P.cos_opp + 1e-5f) {
+        const float sim = __fmul_rn(P.eta, fmaxf(qxc, P.eps_q));
+        for (int j0 = 0; j0 < T.count; j0 += 32) {
+          // stop once a candidate is held and this chunk starts beyond its shell
+          if (best != ~0ull && (int)T.o[j0].d2 > (int)(best >> 40)) break;
+          const int j = j0 + lane;
+          unsigned long long key = ~0ull;
+          if (j < T.count) {
+            const NciOffset o = T.o[j];
+            const int yb = ob + o.dx + G::HX * (o.dy + G::HY * o.dz);
+            const float qy = q_gate_value(s_phi[yb]);
+            if (qy >= P.q_th && fabsf(__fsub_rn(qy, qxc)) <= sim) {
+              const float dot = __fadd_rn(__fadd_rn(__fmul_rn(n0, s_n[yb]), __fmul_rn(n1, s_n[G::NB + yb])),
+                                          __fmul_rn(n2, s_n[2 * G::NB + yb]));
+              if (dot <= P.cos_opp) {
+                const float ff = fmaxf(-dot, 0.0f);
+                key = ((unsigned long long)o.d2 << 40) |
+                      ((unsigned long long)(0x7fffffffu - __float_as_uint(ff)) << 9) | (unsigned long long)j;
+              }
+            }
+          }
+          if (__any_sync(0xffffffffu, key != ~0ull)) {
+#pragma unroll
+            for (int sh = 16; sh > 0; sh >>= 1) {
+              const unsigned long long other = __shfl_xor_sync(0xffffffffu, key, sh);
+              key = other < key ? other : key;
+            }
+            best = key < best ? key : best;
+          }
+        }
+      }
+      if (lane != 0) continue;
+      const long long gidx = (long long)(x0 + cx) + (long long)nx * ((y0 + cy) + (long long)ny * (z0 + cz));
+      float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (best != ~0ull) {
+        const int bj = (int)(best & 511ull);
+        const NciOffset o = T.o[bj];
+        const float ff = __uint_as_float(0x7fffffffu - (unsigned)((best >> 9) & 0x7fffffffull));
+        const int yb = ob + o.dx + G::HX * (o.dy + G::HY * o.dz);
+        const int32_t vy = s_phi[yb];
+        const float m0 = s_n[yb], m1 = s_n[G::NB + yb], m2 = s_n[2 * G::NB + yb];
+        const float qy = q_gate_value(vy);
+        // paired indicator and clamp, Eqs. 66-67
+        const float qpair = 0.5f * (qxc + qy);
+        const float qcl = fminf(fmaxf(qpair, P.eps_q), 0.25f - P.eps_q);
+        // proximity indicator, Eq. 70, as eps * artanh(sqrt(1 - 4 q)): the same value, and
+        // 1 - 4 q_pair = ((1 - 2 phi_x)^2 + (1 - 2 phi_y)^2) / 2 has no cancellation
+        float mm;
+        if (qcl == qpair) {
+          const float ax = 1.0f - 2.0f * fminf(fmaxf(phi_of(vx), 0.f), 1.f);
+          const float ay = 1.0f - 2.0f * fminf(fmaxf(phi_of(vy), 0.f), 1.f);
+          mm = 0.5f * (ax * ax + ay * ay);
+        } else {
+          mm = 1.0f - 4.0f * qcl;
+        }
+        const float h = P.eps * atanhf(sqrtf(mm));
+        const float tt = h / P.h0;
+        const float tp = (P.p == 4.0f) ? (tt * tt) * (tt * tt) : powf(tt, P.p);
+        const float wh = 1.0f / (1.0f + tp);  // Eq. 71
+        // symmetric normal, Eq. 69, line-of-centres fallback, oriented toward the partner
+        const float rn = sqrtf((float)o.d2);
+        const float r0 = o.dx / rn, r1 = o.dy / rn, r2 = o.dz / rn;
+        float s0 = n0 - m0, s1 = n1 - m1, s2 = n2 - m2;
+        const float sn = sqrtf(s0 * s0 + s1 * s1 + s2 * s2);
+        if (sn < 1e-8f) {
+          s0 = r0; s1 = r1; s2 = r2;
+        } else {
+          const float is = 1.0f / (sn + P.eps_n);
+          s0 *= is; s1 *= is; s2 *= is;
+        }
+        if (r0 * s0 + r1 * s1 + r2 * s2 < 0.0f) {
+          s0 = -s0; s1 = -s1; s2 = -s2;
+        }
+        // flux and force density with the facing factor of Eq. 68, Eqs. 72-73
+        const float rho = P.rho_g + P.drho * phi_of(vx);
+        const float amp = rho * P.A_rep * qcl * wh * ff;
+        out = make_float4(amp * s0, amp * s1, DIM == 3 ? amp * s2 : 0.0f, 1.0f);
+        if (partner) {
+          partner[3 * gidx] = o.dx;
+          partner[3 * gidx + 1] = o.dy;
+          partner[3 * gidx + 2] = o.dz;
+        }
+      } else if (partner) {
+        partner[3 * gidx] = partner[3 * gidx + 1] = partner[3 * gidx + 2] = INT32_MIN;
+      }
+      frep[gidx] = out;
+    }
+    __syncthreads();  // the next tile reuses the shared buffers
   }
 }
 
@@ -238,34 +283,32 @@ static cudaError_t nci_attr() {
   using G = NciGeom<DIM>;
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_nci_full<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_nci_list<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem);
+  cudaError_t e = cudaFuncSetAttribute(k_nci_scan<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem);
   if (e == cudaSuccess) done = true;
   return e;
 }
 
 template <int DIM>
-static cudaError_t launch_nci_dim(const KParams &P, const NciTable &T, const int32_t *phi, float4 *frep,
+static cudaError_t launch_nci_dim(const KParams &P, const NciTable &T, const int32_t *phi, float4 *nrm, float4 *frep,
                                   int32_t *partner, int debug, const int *tiles, const int *ntiles, int list_blocks,
                                   cudaStream_t s) {
   using G = NciGeom<DIM>;
   cudaError_t e = nci_attr<DIM>();
   if (e != cudaSuccess) return e;
+  const int gtx = (P.nx + G::TX - 1) / G::TX, gty = (P.ny + G::TY - 1) / G::TY, gtz = (P.nz + G::TZ - 1) / G::TZ;
+  const int total = gtx * gty * gtz;
+  const int blocks = tiles ? list_blocks : (total < list_blocks * 4 ? total : list_blocks * 4);
   dim3 block(G::TX, G::TY, G::TZ);
-  dim3 grid((P.nx + G::TX - 1) / G::TX, (P.ny + G::TY - 1) / G::TY, (P.nz + G::TZ - 1) / G::TZ);
-  if (tiles)
-    k_nci_list<DIM><<<list_blocks, block, G::smem, s>>>(P, T, phi, frep, tiles, ntiles, grid.x, grid.y);
-  else
-    k_nci_full<DIM><<<grid, block, G::smem, s>>>(P, T, phi, frep, partner, debug);
+  k_nci_normals<DIM><<<blocks, block, 0, s>>>(P, phi, nrm, tiles, ntiles, total, gtx, gty);
+  k_nci_scan<DIM><<<blocks, block, G::smem, s>>>(P, T, phi, nrm, frep, partner, debug, tiles, ntiles, total, gtx, gty);
   return cudaGetLastError();
 }
 
-cudaError_t launch_nci(int dim, const KParams &P, const NciTable &T, const int32_t *phi, float4 *frep,
+cudaError_t launch_nci(int dim, const KParams &P, const NciTable &T, const int32_t *phi, float4 *nrm, float4 *frep,
                        int32_t *partner, int debug, const int *tiles, const int *ntiles, int list_blocks,
                        cudaStream_t s) {
-  return dim == 2 ? launch_nci_dim<2>(P, T, phi, frep, partner, debug, tiles, ntiles, list_blocks, s)
-                  : launch_nci_dim<3>(P, T, phi, frep, partner, debug, tiles, ntiles, list_blocks, s);
+  return dim == 2 ? launch_nci_dim<2>(P, T, phi, nrm, frep, partner, debug, tiles, ntiles, list_blocks, s)
+                  : launch_nci_dim<3>(P, T, phi, nrm, frep, partner, debug, tiles, ntiles, list_blocks, s);
 }
 
 int nci_list_blocks(int dim) {
@@ -274,10 +317,10 @@ int nci_list_blocks(int dim) {
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   if (dim == 2) {
     if (nci_attr<2>() != cudaSuccess) return 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_nci_list<2>, NciGeom<2>::NT, NciGeom<2>::smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_nci_scan<2>, NciGeom<2>::NT, NciGeom<2>::smem);
   } else {
     if (nci_attr<3>() != cudaSuccess) return 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_nci_list<3>, NciGeom<3>::NT, NciGeom<3>::smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_nci_scan<3>, NciGeom<3>::NT, NciGeom<3>::smem);
   }
   return sms * (per > 0 ? per : 1);
 }

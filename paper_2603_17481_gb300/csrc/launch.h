@@ -14,9 +14,10 @@ struct NciTable {
 // Kernel modes of the hydrodynamic kernel.
 enum HydroMode { kStep = 0, kMoments = 1 };
 
+// Normals of the gated cells into nrm, then the window scan writing frep at gated cells.
 // tiles == nullptr: every tile (debug = 1 also writes zero force / no partner at every cell);
 // otherwise only the ntiles listed tiles, walked by list_blocks resident blocks.
-cudaError_t launch_nci(int dim, const KParams &P, const NciTable &T, const int32_t *phi, float4 *frep,
+cudaError_t launch_nci(int dim, const KParams &P, const NciTable &T, const int32_t *phi, float4 *nrm, float4 *frep,
                        int32_t *partner, int debug, const int *tiles, const int *ntiles, int list_blocks,
                        cudaStream_t s);
 int nci_list_blocks(int dim);

@@ -6,6 +6,7 @@
 //   phi[2]   N int32      fixed-point phi, ping-pong
 //   u        3*N float    velocity of the last hydrodynamic pass (advects phi)
 //   frep     N float4     near-contact force, valid at gated cells only
+//   nrm      N float4     interface normals, valid at gated cells only
 //   mom      4*N float    u and p* of lbm_read_fields / lbm_mass (allocated on first use)
 //   stage    k*N double   FP64 staging of host I/O (allocated on first use, grown as needed)
 //   tiles[2] int          near-contact tiles holding an interfacial cell of phi[k] (+ 2 counts)
@@ -182,7 +183,7 @@ int run_moments(lbm_ctx *c) {
   const int d = c->P.dim;
   if (c->P.nci_on) {
     rc = from_cuda(timed(c, LBM_K_NCI, [&] {
-      return launch_nci(d, c->K, c->T, c->phi[c->pcur], c->frep, nullptr, 0, c->tiles[c->pcur],
+      return launch_nci(d, c->K, c->T, c->phi[c->pcur], c->nrm, c->frep, nullptr, 0, c->tiles[c->pcur],
                         c->ntiles + c->pcur, c->nci_blocks, c->stream);
     }));
     if (rc) return rc;
@@ -226,6 +227,7 @@ int lbm_create(const lbm_params *p, lbm_ctx **out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->phi[1], sizeof(int32_t) * c->N);
   if (e == cudaSuccess) e = cudaMalloc(&c->u, sizeof(float) * 3 * c->N);
   if (e == cudaSuccess) e = cudaMalloc(&c->frep, sizeof(float4) * c->N);
+  if (e == cudaSuccess) e = cudaMalloc(&c->nrm, sizeof(float4) * c->N);
   const int ntile = tile_count(p->dim, c->K);
   if (e == cudaSuccess) e = cudaMalloc(&c->tiles[0], sizeof(int) * ntile);
   if (e == cudaSuccess) e = cudaMalloc(&c->tiles[1], sizeof(int) * ntile);
@@ -259,7 +261,7 @@ void lbm_destroy(lbm_ctx *c) {
   for (auto e : c->pool) cudaEventDestroy(e);
   cudaFree(c->pop[0]); cudaFree(c->pop[1]);
   cudaFree(c->phi[0]); cudaFree(c->phi[1]);
-  cudaFree(c->u); cudaFree(c->frep); cudaFree(c->mom); cudaFree(c->stage);
+  cudaFree(c->u); cudaFree(c->frep); cudaFree(c->nrm); cudaFree(c->mom); cudaFree(c->stage);
   cudaFree(c->partner); cudaFree(c->red_part); cudaFree(c->red_out);
   cudaFree(c->tiles[0]); cudaFree(c->tiles[1]); cudaFree(c->ntiles);
   delete c;
@@ -342,7 +344,7 @@ int lbm_step(lbm_ctx *c, int n) {
     const bool nci = c->P.nci_on != 0;
     if (nci) {
       rc = from_cuda(timed(c, LBM_K_NCI, [&] {
-        return launch_nci(d, c->K, c->T, c->phi[c->pcur], c->frep, nullptr, 0, c->tiles[c->pcur],
+        return launch_nci(d, c->K, c->T, c->phi[c->pcur], c->nrm, c->frep, nullptr, 0, c->tiles[c->pcur],
                           c->ntiles + c->pcur, c->nci_blocks, c->stream);
       }));
       if (rc) return rc;
@@ -435,7 +437,8 @@ int lbm_read_nci(lbm_ctx *c, int32_t *partner, double *frep) {
   }
   if ((rc = ensure_stage(c, sizeof(double) * 3 * N))) return rc;
   rc = from_cuda(timed(c, LBM_K_NCI, [&] {
-    return launch_nci(c->P.dim, c->K, c->T, c->phi[c->pcur], c->frep, c->partner, 1, nullptr, nullptr, 0, c->stream);
+    return launch_nci(c->P.dim, c->K, c->T, c->phi[c->pcur], c->nrm, c->frep, c->partner, 1, nullptr, nullptr,
+                      c->nci_blocks, c->stream);
   }));
   if (rc) return rc;
   if (partner && (rc = d2h(c, partner, c->partner, sizeof(int32_t) * 3 * N))) return rc;
