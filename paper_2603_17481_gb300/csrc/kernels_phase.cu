@@ -223,6 +223,262 @@ k_phase(const KParams P, const int32_t *__restrict__ phi, const float *__restric
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// 3D: a block owns a 32 x 8 column of cells over ZC planes and marches along z, keeping ring
+// buffers of planes in shared memory. The D3Q27 weights factor as s(c_x) s(c_y) s(c_z) / 216, so
+//   RZ(k)   = phi(k-1) + 4 phi(k) + phi(k+1)         (exact, 64-bit)
+//   PSXY(k) = s_x s_y phi(k)                         (exact, 64-bit)
+//   grad_x phi = (1/72) s_y [RZ(x+1) - RZ(x-1)],  grad_y phi = (1/72) s_x [RZ(y+1) - RZ(y-1)],
+//   grad_z phi = (1/72) [PSXY(k+1) - PSXY(k-1)],
+// and the face transfers of the header use the same planes: B_x (phi(p) - phi(p+e)) =
+// (1/36) s_y [RZ(p) - RZ(p+e)], B_y (...) = (1/6) [RZ(p) - RZ(p+e)], and the compressive sums
+// s_y s_z a_x, s_x s_z a_y, s_x s_y a_z from the z-smoothed planes AXZ, AYZ and the in-plane ASXY.
+// Every a value and every face transfer is computed once per block; the faces on block borders
+// are computed by both neighbours from identical inputs with the same rounded operations.
+// ---------------------------------------------------------------------------------------------
+struct Phase3 {
+  static constexpr int TX = 32, TY = 8, ZC = 16, NT = TX * TY;
+  static constexpr int PX = TX + 4, PY = TY + 4, NP = PX * PY;  // phi / RZ planes (halo 2)
+  static constexpr int QX = TX + 2, QY = TY + 2, NQ = QX * QY;  // PSXY / a planes (halo 1)
+  static constexpr int NC = TX * TY;
+  static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
+  static constexpr int NFLG = (ZC / 4) * (TY / 4);
+  static constexpr size_t smem = sizeof(long long) * (2 * NP + 4 * NQ) + sizeof(int32_t) * 4 * NP +
+                                 sizeof(float) * (12 * NQ + 2 * NQ + 2 * NC + QX * TY + TX * QY + 2 * NC) +
+                                 sizeof(int32_t) * (NFX + NFY + 2 * NC + NFLG);
+  __device__ static __forceinline__ int pi(int lx, int ly) { return (ly + 2) * PX + lx + 2; }
+  __device__ static __forceinline__ int qi(int lx, int ly) { return (ly + 1) * QX + lx + 1; }
+};
+
+__device__ __forceinline__ long long s141(long long a, long long b, long long c) { return a + 4 * b + c; }
+
+__global__ void __launch_bounds__(Phase3::NT, 4)
+k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restrict__ u,
+         int32_t *__restrict__ phi_out, int *__restrict__ tiles, int *__restrict__ ntiles) {
+  using G = Phase3;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  long long *RZ = reinterpret_cast<long long *>(smem_raw);  // [2][NP]
+  long long *PS = RZ + 2 * G::NP;                            // [4][NQ]
+  int32_t *PH = reinterpret_cast<int32_t *>(PS + 4 * G::NQ);  // [4][NP]
+  float *A = reinterpret_cast<float *>(PH + 4 * G::NP);       // [4][3][NQ]
+  float *AXZ = A + 12 * G::NQ;                               // [NQ]
+  float *AYZ = AXZ + G::NQ;                                  // [NQ]
+  float *ASXY = AYZ + G::NQ;                                 // [2][NC]
+  float *UX = ASXY + 2 * G::NC;                              // [TY][QX]: lx -1..32
+  float *UY = UX + G::QX * G::TY;                            // [QY][TX]: ly -1..8
+  float *UZ = UY + G::TX * G::QY;                            // [2][NC]
+  int32_t *TXF = reinterpret_cast<int32_t *>(UZ + 2 * G::NC);  // [TY][TX+1]
+  int32_t *TYF = TXF + G::NFX;                                 // [TY+1][TX]
+  int32_t *TZF = TYF + G::NFY;                                 // [2][NC]
+  int *FLG = TZF + 2 * G::NC;                                  // near-contact tile flags
+
+  const int lane = threadIdx.x, wy = threadIdx.y, tid = lane + 32 * wy;
+  const int nx = P.nx, ny = P.ny, nz = P.nz;
+  const long long N = P.N;
+  const int x0 = blockIdx.x * G::TX, y0 = blockIdx.y * G::TY;
+  const int zb = blockIdx.z * G::ZC, ze = min(zb + G::ZC, nz);
+  const float D = P.Dlap * (1.0f / 6.0f);
+  const float k3 = P.kc * kCs2 * 3.0f;  // 3 kappa
+  // this thread's x columns for plane loads: phi planes (lx = lane - 2, and 30..33 for lanes 0..3),
+  // u_x planes (lx = lane - 1, and 31..32 for lanes 0..1)
+  const int xa = wrapn(x0 + lane - 2, nx), xb = wrapn(x0 + 30 + (lane & 3), nx);
+  const int ua = wrapn(x0 + lane - 1, nx), ub = wrapn(x0 + 31 + (lane & 1), nx);
+  if (tid < G::NFLG) FLG[tid] = 0;
+
+  // Plane loads are software-pipelined: the values for iteration k + 1 (phi plane k + 3, u_z plane
+  // k + 2, u_x and u_y planes k + 1) are loaded into registers during iteration k.
+  int32_t rphi[4];
+  float ruz, rux[2], ruy[2];
+  auto prefetch = [&](int kk) {
+    const int Z = wrapn(kk + 2, nz);
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int r = wy + h * G::TY;
+      if (r < G::PY) {
+        const long long row = (long long)nx * (wrapn(y0 + r - 2, ny) + (long long)ny * Z);
+        rphi[2 * h] = phi[row + xa];
+        if (lane < 4) rphi[2 * h + 1] = phi[row + xb];
+      }
+    }
+    const int Zu = wrapn(kk + 1, nz), Zk = wrapn(kk, nz);
+    const int xc = wrapn(x0 + lane, nx);
+    ruz = __ldg(u + 2 * N + (long long)nx * (wrapn(y0 + wy, ny) + (long long)ny * Zu) + xc);
+    const long long rowk = (long long)nx * (wrapn(y0 + wy, ny) + (long long)ny * Zk);
+    rux[0] = __ldg(u + rowk + ua);
+    if (lane < 2) rux[1] = __ldg(u + rowk + ub);
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int r = wy + h * G::TY;
+      if (r < G::QY) ruy[h] = __ldg(u + N + (long long)nx * (wrapn(y0 + r - 1, ny) + (long long)ny * Zk) + xc);
+    }
+  };
+  prefetch(zb - 4);
+
+  for (int k = zb - 4; k < ze; k++) {
+    const int s4k = (k + 8) & 3, s4k1 = (k + 9) & 3, s4k2 = (k + 10) & 3, s4km = (k + 7) & 3;
+    // S1: phi plane k+2; u_z plane k+1; u_x, u_y planes k (from registers), then prefetch k+1
+    {
+      int32_t *ph = PH + s4k2 * G::NP;
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int r = wy + h * G::TY;
+        if (r < G::PY) {
+          ph[r * G::PX + lane] = rphi[2 * h];
+          if (lane < 4) ph[r * G::PX + 32 + lane] = rphi[2 * h + 1];
+        }
+      }
+      UZ[((k + 1) & 1) * G::NC + tid] = ruz;
+      UX[wy * G::QX + lane] = rux[0];
+      if (lane < 2) UX[wy * G::QX + 32 + lane] = rux[1];
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int r = wy + h * G::TY;
+        if (r < G::QY) UY[r * G::TX + lane] = ruy[h];
+      }
+      if (k + 1 < ze) prefetch(k + 1);
+    }
+    __syncthreads();
+    // S2: RZ(k+1) and PSXY(k+2)
+    {
+      const int32_t *p0 = PH + s4k * G::NP, *p1 = PH + s4k1 * G::NP, *p2 = PH + s4k2 * G::NP;
+      if (k >= zb - 2) {
+        long long *rz = RZ + ((k + 1) & 1) * G::NP;
+        for (int t = tid; t < G::NP; t += G::NT) rz[t] = s141(p0[t], p1[t], p2[t]);
+      }
+      long long *ps = PS + s4k2 * G::NQ;
+      for (int t = tid; t < G::NQ; t += G::NT) {
+        const int c = G::pi(t % G::QX - 1, t / G::QX - 1);
+        const long long r0 = s141(p2[c - G::PX - 1], p2[c - G::PX], p2[c - G::PX + 1]);
+        const long long r1 = s141(p2[c - 1], p2[c], p2[c + 1]);
+        const long long r2 = s141(p2[c + G::PX - 1], p2[c + G::PX], p2[c + G::PX + 1]);
+        ps[t] = s141(r0, r1, r2);
+      }
+    }
+    __syncthreads();
+    // S3: a(k+1) = phi (1 - phi) grad(phi) / (|grad(phi)| + eps_n)
+    if (k >= zb - 2) {
+      const long long *rz = RZ + ((k + 1) & 1) * G::NP;
+      const long long *psp = PS + s4k2 * G::NQ, *psm = PS + s4k * G::NQ;
+      const int32_t *p1 = PH + s4k1 * G::NP;
+      float *a = A + s4k1 * 3 * G::NQ;
+      const float gs = kInvQ30 * (1.0f / 72.0f);
+      for (int t = tid; t < G::NQ; t += G::NT) {
+        const int c = G::pi(t % G::QX - 1, t / G::QX - 1);
+        const long long gxi = s141(rz[c - G::PX + 1] - rz[c - G::PX - 1], rz[c + 1] - rz[c - 1],
+                                   rz[c + G::PX + 1] - rz[c + G::PX - 1]);
+        const long long gyi = s141(rz[c + G::PX - 1] - rz[c - G::PX - 1], rz[c + G::PX] - rz[c - G::PX],
+                                   rz[c + G::PX + 1] - rz[c - G::PX + 1]);
+        const long long gzi = psp[t] - psm[t];
+        const float g0 = __ll2float_rn(gxi) * gs, g1 = __ll2float_rn(gyi) * gs, g2 = __ll2float_rn(gzi) * gs;
+        const float ph = phi_of(p1[c]);
+        const float sc = ph * (1.0f - ph) / (sqrtf(g0 * g0 + g1 * g1 + g2 * g2) + P.eps_n);
+        a[t] = g0 * sc;
+        a[G::NQ + t] = g1 * sc;
+        a[2 * G::NQ + t] = g2 * sc;
+      }
+    }
+    __syncthreads();
+    // S4: z-smoothed compressive components at plane k, in-plane s_x s_y a_z at plane k+1
+    if (k >= zb - 2) {
+      const float *az = A + s4k1 * 3 * G::NQ + 2 * G::NQ;
+      float *asxy = ASXY + ((k + 1) & 1) * G::NC;
+      {
+        const int lx = tid & 31, ly = tid >> 5;
+        const int c = G::qi(lx, ly);
+        const float r0 = __fadd_rn(__fadd_rn(az[c - G::QX - 1], __fmul_rn(4.f, az[c - G::QX])), az[c - G::QX + 1]);
+        const float r1 = __fadd_rn(__fadd_rn(az[c - 1], __fmul_rn(4.f, az[c])), az[c + 1]);
+        const float r2 = __fadd_rn(__fadd_rn(az[c + G::QX - 1], __fmul_rn(4.f, az[c + G::QX])), az[c + G::QX + 1]);
+        asxy[tid] = __fadd_rn(__fadd_rn(r0, __fmul_rn(4.f, r1)), r2);
+      }
+      if (k >= zb) {
+        const float *am = A + s4km * 3 * G::NQ, *a0 = A + s4k * 3 * G::NQ, *ap = A + s4k1 * 3 * G::NQ;
+        for (int t = tid; t < G::NQ; t += G::NT) {
+          AXZ[t] = __fadd_rn(__fadd_rn(am[t], __fmul_rn(4.f, a0[t])), ap[t]);
+          AYZ[t] = __fadd_rn(__fadd_rn(am[G::NQ + t], __fmul_rn(4.f, a0[G::NQ + t])), ap[G::NQ + t]);
+        }
+      }
+    }
+    __syncthreads();
+    // S5: face transfers. x and y faces of plane k; z face between planes k and k+1
+    {
+      const int32_t *p0 = PH + s4k * G::NP;
+      if (k >= zb) {
+        const long long *rz = RZ + (k & 1) * G::NP;
+        const float dx_s = kInvQ30 * (1.0f / 36.0f), dy_s = kInvQ30 * (1.0f / 6.0f);
+        for (int t = tid; t < G::NFX; t += G::NT) {
+          const int lx = t % (G::TX + 1) - 1, ly = t / (G::TX + 1);
+          const int c = G::pi(lx, ly);
+          const long long di = s141(rz[c - G::PX] - rz[c - G::PX + 1], rz[c] - rz[c + 1],
+                                    rz[c + G::PX] - rz[c + G::PX + 1]);
+          float tau = __fmul_rn(D, __fmul_rn(__ll2float_rn(di), dx_s));
+          const int q = G::qi(lx, ly);
+          const float cs = __fadd_rn(__fadd_rn(__fadd_rn(AXZ[q - G::QX], AXZ[q - G::QX + 1]),
+                                               __fmul_rn(4.f, __fadd_rn(AXZ[q], AXZ[q + 1]))),
+                                     __fadd_rn(AXZ[q + G::QX], AXZ[q + G::QX + 1]));
+          tau = __fadd_rn(tau, __fmul_rn(k3, __fmul_rn(cs, 1.0f / 216.0f)));
+          const int32_t vm = p0[c - 1], v0 = p0[c], v1 = p0[c + 1], vp = p0[c + 2];
+          const int32_t sl = minmod_i(v0 - vm, v1 - v0), sr = minmod_i(v1 - v0, vp - v1);
+          const float uf = __fmul_rn(0.5f, __fadd_rn(UX[ly * G::QX + lx + 1], UX[ly * G::QX + lx + 2]));
+          const long long up2 = uf >= 0.0f ? 2LL * v0 + sl : 2LL * v1 - sr;
+          tau = __fadd_rn(tau, __fmul_rn(uf, __ll2float_rn(up2) * (0.5f * kInvQ30)));
+          TXF[t] = __float2int_rn(__fmul_rn(tau, kQ30));
+        }
+        for (int t = tid; t < G::NFY; t += G::NT) {
+          const int lx = t % G::TX, ly = t / G::TX - 1;
+          const int c = G::pi(lx, ly);
+          float tau = __fmul_rn(D, __fmul_rn(__ll2float_rn(rz[c] - rz[c + G::PX]), dy_s));
+          const int q = G::qi(lx, ly);
+          const float cs = __fadd_rn(__fadd_rn(__fadd_rn(AYZ[q - 1], AYZ[q - 1 + G::QX]),
+                                               __fmul_rn(4.f, __fadd_rn(AYZ[q], AYZ[q + G::QX]))),
+                                     __fadd_rn(AYZ[q + 1], AYZ[q + 1 + G::QX]));
+          tau = __fadd_rn(tau, __fmul_rn(k3, __fmul_rn(cs, 1.0f / 216.0f)));
+          const int32_t vm = p0[c - G::PX], v0 = p0[c], v1 = p0[c + G::PX], vp = p0[c + 2 * G::PX];
+          const int32_t sl = minmod_i(v0 - vm, v1 - v0), sr = minmod_i(v1 - v0, vp - v1);
+          const float uf = __fmul_rn(0.5f, __fadd_rn(UY[(ly + 1) * G::TX + lx], UY[(ly + 2) * G::TX + lx]));
+          const long long up2 = uf >= 0.0f ? 2LL * v0 + sl : 2LL * v1 - sr;
+          tau = __fadd_rn(tau, __fmul_rn(uf, __ll2float_rn(up2) * (0.5f * kInvQ30)));
+          TYF[t] = __float2int_rn(__fmul_rn(tau, kQ30));
+        }
+      }
+      if (k >= zb - 1) {
+        const int lx = tid & 31, ly = tid >> 5;
+        const int c = G::pi(lx, ly);
+        const int32_t vm = PH[s4km * G::NP + c], v0 = p0[c], v1 = PH[s4k1 * G::NP + c], vp = PH[s4k2 * G::NP + c];
+        float tau = __fmul_rn(D, dphi_of(v0, v1));
+        const float cs = __fadd_rn(ASXY[(k & 1) * G::NC + tid], ASXY[((k + 1) & 1) * G::NC + tid]);
+        tau = __fadd_rn(tau, __fmul_rn(k3, __fmul_rn(cs, 1.0f / 216.0f)));
+        const int32_t sl = minmod_i(v0 - vm, v1 - v0), sr = minmod_i(v1 - v0, vp - v1);
+        const float uf = __fmul_rn(0.5f, __fadd_rn(UZ[(k & 1) * G::NC + tid], UZ[((k + 1) & 1) * G::NC + tid]));
+        const long long up2 = uf >= 0.0f ? 2LL * v0 + sl : 2LL * v1 - sr;
+        tau = __fadd_rn(tau, __fmul_rn(uf, __ll2float_rn(up2) * (0.5f * kInvQ30)));
+        TZF[((k + 1) & 1) * G::NC + tid] = __float2int_rn(__fmul_rn(tau, kQ30));
+      }
+    }
+    __syncthreads();
+    // S6: phi^{n+1} of plane k
+    if (k >= zb) {
+      const int lx = tid & 31, ly = tid >> 5;
+      const int x = x0 + lx, y = y0 + ly;
+      if (x < nx && y < ny) {
+        int32_t acc = TXF[ly * (G::TX + 1) + lx] - TXF[ly * (G::TX + 1) + lx + 1];
+        acc += TYF[ly * G::TX + lx] - TYF[(ly + 1) * G::TX + lx];
+        acc += TZF[(k & 1) * G::NC + tid] - TZF[((k + 1) & 1) * G::NC + tid];
+        const int32_t vn = PH[s4k * G::NP + G::pi(lx, ly)] + acc;
+        phi_out[(long long)x + (long long)nx * (y + (long long)ny * k)] = vn;
+        if (tiles && q_gate_value(vn) >= P.q_th) FLG[((k - zb) >> 2) * (G::TY / 4) + (ly >> 2)] = 1;
+      }
+    }
+  }
+  if (tiles) {
+    __syncthreads();
+    if (tid < G::NFLG && FLG[tid]) {
+      const int gtx = (nx + 31) / 32, gty = (ny + 3) / 4;
+      const int bzt = zb / 4 + tid / (G::TY / 4), byt = y0 / 4 + tid % (G::TY / 4);
+      tiles[atomicAdd(ntiles, 1)] = blockIdx.x + gtx * (byt + gty * bzt);
+    }
+  }
+}
+
 template <int DIM>
 static cudaError_t launch_phase_dim(const KParams &P, const int32_t *phi, const float *u, int32_t *phi_out,
                                     int *tiles, int *ntiles, cudaStream_t s) {
@@ -233,10 +489,24 @@ static cudaError_t launch_phase_dim(const KParams &P, const int32_t *phi, const 
   return cudaGetLastError();
 }
 
+static cudaError_t launch_phase3(const KParams &P, const int32_t *phi, const float *u, int32_t *phi_out, int *tiles,
+                                 int *ntiles, cudaStream_t s) {
+  using G = Phase3;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_phase3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((P.nx + G::TX - 1) / G::TX, (P.ny + G::TY - 1) / G::TY, (P.nz + G::ZC - 1) / G::ZC);
+  k_phase3<<<grid, dim3(32, G::TY), G::smem, s>>>(P, phi, u, phi_out, tiles, ntiles);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_phase(int dim, const KParams &P, const int32_t *phi, const float *u, int32_t *phi_out,
                          int *tiles, int *ntiles, cudaStream_t s) {
   return dim == 2 ? launch_phase_dim<2>(P, phi, u, phi_out, tiles, ntiles, s)
-                  : launch_phase_dim<3>(P, phi, u, phi_out, tiles, ntiles, s);
+                  : launch_phase3(P, phi, u, phi_out, tiles, ntiles, s);
 }
 
 // Lists the tiles holding an interfacial cell of phi (used after the state is set from the host).
