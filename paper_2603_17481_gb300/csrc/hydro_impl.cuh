@@ -8,7 +8,8 @@
 // One thread per cell, 32 consecutive x per warp (coalesced stores, loads offset by one cell).
 // Each thread wraps its neighbour coordinates once per axis and forms the 9 (3D) or 3 (2D) row
 // offsets of its neighbourhood, so a pull address is one add. phi of the tile + 1 halo is staged
-// in shared memory row by row as fixed-point integers; stencil differences are exact integers.
+// in shared memory row by row, converted once to FP32 (the interfacial gate of the cell itself is
+// taken on the stored fixed-point value, as in the near-contact kernel).
 //
 // The collision is evaluated from moments rather than by summing over tensors: with the
 // fourth-order isotropy of D2Q9/D3Q19/D3Q27, sum f_eq c c = p* cs^2 I + u u and sum S c c =
@@ -40,7 +41,7 @@ k_hydro(const KParams P, const typename Store<S>::T *__restrict__ src, typename 
   static_assert(TT::X == 32, "one warp per x row");
   constexpr int HX = TT::X + 2, HY = TT::Y + 2, HZ = DIM == 3 ? TT::Z + 2 : 1;
   constexpr int NROWS = HY * HZ, NWARPS = TT::Y * TT::Z;
-  __shared__ int32_t s_phi[NROWS * HX];
+  __shared__ float s_phi[NROWS * HX];
 
   const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
   const int nx = P.nx, ny = P.ny, nz = P.nz;
@@ -57,8 +58,8 @@ k_hydro(const KParams P, const typename Store<S>::T *__restrict__ src, typename 
       const int Y = wrapn(y0 + ry - 1, ny);
       const int Z = DIM == 3 ? wrapn(z0 + rz - 1, nz) : 0;
       const int32_t *row = phi + (long long)nx * (Y + (long long)ny * Z);
-      s_phi[r * HX + tx] = row[xl];
-      if (tx < 2) s_phi[r * HX + 32 + tx] = row[xr];
+      s_phi[r * HX + tx] = phi_of(row[xl]);
+      if (tx < 2) s_phi[r * HX + 32 + tx] = phi_of(row[xr]);
     }
   }
   __syncthreads();
@@ -89,24 +90,24 @@ k_hydro(const KParams P, const typename Store<S>::T *__restrict__ src, typename 
     f[i] = Store<S>::ld(src + (long long)i * N + s, L::w(i));
   }
 
-  // isotropic gradient and Laplacian of phi (Eqs. 22-23) on exact fixed-point differences
+  // isotropic gradient and Laplacian of phi (Eqs. 22-23)
   const int b = (DIM == 3 ? (tz + 1) * HX * HY : 0) + (ty + 1) * HX + tx + 1;
-  const int32_t v = s_phi[b];
+  const int32_t v = __ldg(phi + idx);
+  const float ph = s_phi[b];
   float g0 = 0.f, g1 = 0.f, g2 = 0.f, lap = 0.f;
 #pragma unroll
   for (int i = 1; i < SL::Q; i++) {
     if (!positive<SL>(i)) continue;
     const int o = SL::c(i, 0) + HX * (SL::c(i, 1) + HY * SL::c(i, 2));
-    const int32_t vp = s_phi[b + o], vm = s_phi[b - o];
-    const float d = SL::w(i) * dphi_of(vp, vm);
+    const float vp = s_phi[b + o], vm = s_phi[b - o];
+    const float d = SL::w(i) * (vp - vm);
     g0 += SL::c(i, 0) * d;
     g1 += SL::c(i, 1) * d;
     if (DIM == 3) g2 += SL::c(i, 2) * d;
-    lap += SL::w(i) * (dphi_of(vp, v) + dphi_of(vm, v));
+    lap += SL::w(i) * ((vp - ph) + (vm - ph));
   }
   g0 *= 3.0f; g1 *= 3.0f; g2 *= 3.0f;  // 1 / cs^2
   lap *= 6.0f;                          // 2 / cs^2
-  const float ph = phi_of(v);
 
   // mixture properties, Eqs. 8-10 (linear rho and mu)
   const float rho = P.rho_g + P.drho * ph;
@@ -191,19 +192,71 @@ k_hydro(const KParams P, const typename Store<S>::T *__restrict__ src, typename 
   const float k45 = 4.5f * om1, k135 = 13.5f * om1, k9 = 9.0f * om1;
 
   Store<S>::st_w(dst + idx, C0, L::w(0));
+  // per pair of opposite directions: c.u, c.F', c.A2.c, c.A2.u; then the even and odd parts are
+  // evaluated two pairs at a time with the packed FP32x2 operations of sm_100+
+  constexpr int NPAIR = (L::Q - 1) / 2;
+  float pcu[NPAIR], pcr[NPAIR], pcac[NPAIR], pcau[NPAIR];
+  {
+    int pp = 0;
 #pragma unroll
-  for (int i = 1; i < L::Q; i++) {
-    if (!(i > L::opp(i))) continue;
-    const int c0 = L::c(i, 0), c1 = L::c(i, 1), c2 = L::c(i, 2);
-    const float cu = c0 * u0 + c1 * u1 + c2 * u2;
-    const float cr = c0 * r0 + c1 * r1 + c2 * r2;
-    const float cAc = c0 * c0 * A00 + c1 * c1 * A11 + c2 * c2 * A22 +
-                      2.0f * (c0 * c1 * A01 + c0 * c2 * A02 + c1 * c2 * A12);
-    const float cAu = c0 * Au0 + c1 * Au1 + c2 * Au2;
-    const float ev = C0 + cu * (4.5f * cu + 4.5f * cr) + k45 * cAc;
-    const float od = cu * (C1 + 4.5f * cu * cu + k135 * cAc) - k9 * cAu + 1.5f * cr;
-    Store<S>::st_w(dst + (long long)i * N + idx, ev + od, L::w(i));
-    Store<S>::st_w(dst + (long long)L::opp(i) * N + idx, ev - od, L::w(i));
+    for (int i = 1; i < L::Q; i++) {
+      if (!(i > L::opp(i))) continue;
+      const int c0 = L::c(i, 0), c1 = L::c(i, 1), c2 = L::c(i, 2);
+      pcu[pp] = c0 * u0 + c1 * u1 + c2 * u2;
+      pcr[pp] = c0 * r0 + c1 * r1 + c2 * r2;
+      pcac[pp] = c0 * c0 * A00 + c1 * c1 * A11 + c2 * c2 * A22 + 2.0f * (c0 * c1 * A01 + c0 * c2 * A02 + c1 * c2 * A12);
+      pcau[pp] = c0 * Au0 + c1 * Au1 + c2 * Au2;
+      pp++;
+    }
+  }
+  const float2 vC0 = make_float2(C0, C0), vC1 = make_float2(C1, C1), v45 = make_float2(4.5f, 4.5f);
+  const float2 vk45 = make_float2(k45, k45), vk135 = make_float2(k135, k135), vmk9 = make_float2(-k9, -k9);
+  const float2 v15 = make_float2(1.5f, 1.5f), vm1 = make_float2(-1.0f, -1.0f);
+#pragma unroll
+  for (int p = 0; p < NPAIR; p += 2) {
+    if (p + 1 < NPAIR) {
+      const float2 cu = make_float2(pcu[p], pcu[p + 1]), cr = make_float2(pcr[p], pcr[p + 1]);
+      const float2 cac = make_float2(pcac[p], pcac[p + 1]), cau = make_float2(pcau[p], pcau[p + 1]);
+      float2 ev = __ffma2_rn(cu, __fmul2_rn(v45, __fadd2_rn(cu, cr)), vC0);
+      ev = __ffma2_rn(vk45, cac, ev);
+      float2 in = __ffma2_rn(v45, __fmul2_rn(cu, cu), vC1);
+      in = __ffma2_rn(vk135, cac, in);
+      float2 od = __ffma2_rn(vmk9, cau, __fmul2_rn(cu, in));
+      od = __ffma2_rn(v15, cr, od);
+      const float2 fpos = __fadd2_rn(ev, od), fneg = __ffma2_rn(vm1, od, ev);
+      // the pair indices of p and p + 1
+      int ia = 0, ib = 0;
+      {
+        int pp = 0;
+#pragma unroll
+        for (int i = 1; i < L::Q; i++) {
+          if (!(i > L::opp(i))) continue;
+          if (pp == p) ia = i;
+          if (pp == p + 1) ib = i;
+          pp++;
+        }
+      }
+      Store<S>::st_w(dst + (long long)ia * N + idx, fpos.x, L::w(ia));
+      Store<S>::st_w(dst + (long long)L::opp(ia) * N + idx, fneg.x, L::w(ia));
+      Store<S>::st_w(dst + (long long)ib * N + idx, fpos.y, L::w(ib));
+      Store<S>::st_w(dst + (long long)L::opp(ib) * N + idx, fneg.y, L::w(ib));
+    } else {
+      const float cu = pcu[p], cr = pcr[p], cAc = pcac[p], cAu = pcau[p];
+      const float ev = C0 + cu * (4.5f * cu + 4.5f * cr) + k45 * cAc;
+      const float od = cu * (C1 + 4.5f * cu * cu + k135 * cAc) - k9 * cAu + 1.5f * cr;
+      int ia = 0;
+      {
+        int pp = 0;
+#pragma unroll
+        for (int i = 1; i < L::Q; i++) {
+          if (!(i > L::opp(i))) continue;
+          if (pp == p) ia = i;
+          pp++;
+        }
+      }
+      Store<S>::st_w(dst + (long long)ia * N + idx, ev + od, L::w(ia));
+      Store<S>::st_w(dst + (long long)L::opp(ia) * N + idx, ev - od, L::w(ia));
+    }
   }
   u_out[idx] = u0;
   u_out[N + idx] = u1;

@@ -25,8 +25,9 @@ template <int DIM> struct NciGeom {
   static constexpr int HX = TX + 2 * H, HY = TY + 2 * H, HZ = DIM == 3 ? TZ + 2 * H : 1;
   static constexpr int NB = HX * HY * HZ;
   static constexpr int NT = TX * TY * TZ, NW = NT / 32;
-  static constexpr size_t smem =
-      sizeof(int32_t) * NB + sizeof(float) * 3 * NB + sizeof(int) * (NT + 1) + sizeof(float) * 6 * (NW + 1);
+  static constexpr size_t smem = sizeof(int32_t) * NB + sizeof(float) * 3 * NB + sizeof(int) * (NT + 1) +
+                                 sizeof(float) * (6 * (NW + 1) + 1) + sizeof(long long) * (HY * HZ + 1) +
+                                 sizeof(int) * HX;
 };
 
 template <int DIM>
@@ -76,7 +77,7 @@ k_nci_normals(const KParams P, const int32_t *__restrict__ phi, float4 *__restri
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(NciGeom<DIM>::NT)
+__global__ void __launch_bounds__(NciGeom<DIM>::NT, 2)
 k_nci_scan(const KParams P, const NciTable T, const int32_t *__restrict__ phi, const float4 *__restrict__ nrm,
            float4 *__restrict__ frep, int32_t *__restrict__ partner, int debug, const int *__restrict__ tiles,
            const int *__restrict__ ntiles, int total, int gtx, int gty) {
@@ -87,6 +88,8 @@ k_nci_scan(const KParams P, const NciTable T, const int32_t *__restrict__ phi, c
   int *s_list = reinterpret_cast<int *>(s_n + 3 * G::NB);
   int *s_count = s_list + G::NT;
   float *s_rng = reinterpret_cast<float *>(s_count + 1);  // [NW + 1][6]
+  long long *s_row = reinterpret_cast<long long *>(s_rng + 6 * (G::NW + 1) + 1);  // [HY * HZ], 8-aligned
+  int *s_col = reinterpret_cast<int *>(s_row + G::HY * G::HZ);                   // [HX]
 
   const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
   const int tid = tx + G::TX * (ty + G::TY * tz), lane = tid & 31, warp = tid >> 5;
@@ -110,32 +113,57 @@ k_nci_scan(const KParams P, const NciTable T, const int32_t *__restrict__ phi, c
       continue;  // uniform over the block
     }
 
-    // stage phi and the gated normals of the tile + 3 halo (rows of HX = TX + 6 values), and the
-    // component ranges of those normals
-    float lo0 = 1e30f, lo1 = 1e30f, lo2 = 1e30f, hi0 = -1e30f, hi1 = -1e30f, hi2 = -1e30f;
+    // stage phi of the tile + 3 halo (rows of HX = TX + 6 values): all rows' loads are issued
+    // before any is stored; the global row offsets and wrapped columns are kept for the normals
     {
+      constexpr int NROWS = G::HY * G::HZ, RPW = (NROWS + G::NW - 1) / G::NW;
       const int xl = wrapn(x0 - G::H + tx, nx);
       const int xr = wrapn(x0 - G::H + 32 + (tx & 7), nx);
-      constexpr int NROWS = G::HY * G::HZ;
-      for (int r = warp; r < NROWS; r += G::NW) {
-        const int ry = r % G::HY, rz = r / G::HY;
-        const int Yr = wrapn(y0 + ry - G::H, ny);
-        const int Zr = DIM == 3 ? wrapn(z0 + rz - G::H, nz) : 0;
-        const long long row = (long long)nx * (Yr + (long long)ny * Zr);
+      if (warp == 0) s_col[lane] = xl;
+      if (warp == 0 && lane < G::HX - 32) s_col[32 + lane] = xr;
+      int32_t va[RPW], vb[RPW];
 #pragma unroll
-        for (int part = 0; part < 2; part++) {
-          if (part == 1 && lane >= G::HX - 32) break;
-          const int col = part == 0 ? lane : 32 + lane;
-          const long long gi = row + (part == 0 ? xl : xr);
-          const int32_t vb = phi[gi];
-          const int b = r * G::HX + col;
-          s_phi[b] = vb;
-          if (q_gate_value(vb) >= P.q_th) {
-            const float4 nb = __ldg(nrm + gi);
-            s_n[b] = nb.x; s_n[G::NB + b] = nb.y; s_n[2 * G::NB + b] = nb.z;
-            lo0 = fminf(lo0, nb.x); lo1 = fminf(lo1, nb.y); lo2 = fminf(lo2, nb.z);
-            hi0 = fmaxf(hi0, nb.x); hi1 = fmaxf(hi1, nb.y); hi2 = fmaxf(hi2, nb.z);
-          }
+      for (int h = 0; h < RPW; h++) {
+        const int r = warp + h * G::NW;
+        if (r < NROWS) {
+          const int ry = r % G::HY, rz = r / G::HY;
+          const long long row = (long long)nx * (wrapn(y0 + ry - G::H, ny) +
+                                                 (long long)ny * (DIM == 3 ? wrapn(z0 + rz - G::H, nz) : 0));
+          if (lane == 0) s_row[r] = row;
+          va[h] = phi[row + xl];
+          if (lane < G::HX - 32) vb[h] = phi[row + xr];
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < RPW; h++) {
+        const int r = warp + h * G::NW;
+        if (r < NROWS) {
+          s_phi[r * G::HX + lane] = va[h];
+          if (lane < G::HX - 32) s_phi[r * G::HX + 32 + lane] = vb[h];
+        }
+      }
+    }
+    __syncthreads();
+    // gated normals of the box (written once per step by k_nci_normals), loads issued in batches
+    float lo0 = 1e30f, lo1 = 1e30f, lo2 = 1e30f, hi0 = -1e30f, hi1 = -1e30f, hi2 = -1e30f;
+    {
+      constexpr int BATCH = 2;
+      for (int t0 = tid; t0 < G::NB; t0 += BATCH * G::NT) {
+        float4 nb[BATCH];
+        bool gb[BATCH];
+#pragma unroll
+        for (int h = 0; h < BATCH; h++) {
+          const int b = t0 + h * G::NT;
+          gb[h] = b < G::NB && q_gate_value(s_phi[b]) >= P.q_th;
+          if (gb[h]) nb[h] = __ldg(nrm + s_row[b / G::HX] + s_col[b % G::HX]);
+        }
+#pragma unroll
+        for (int h = 0; h < BATCH; h++) {
+          if (!gb[h]) continue;
+          const int b = t0 + h * G::NT;
+          s_n[b] = nb[h].x; s_n[G::NB + b] = nb[h].y; s_n[2 * G::NB + b] = nb[h].z;
+          lo0 = fminf(lo0, nb[h].x); lo1 = fminf(lo1, nb[h].y); lo2 = fminf(lo2, nb[h].z);
+          hi0 = fmaxf(hi0, nb[h].x); hi1 = fmaxf(hi1, nb[h].y); hi2 = fmaxf(hi2, nb[h].z);
         }
       }
     }
