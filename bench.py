@@ -324,6 +324,103 @@ def run_ours(args, world, rank, local):
     return line
 
 
+SWEEP_WORKLOAD = ("batched sweep: {n} independent 3D D3Q19 collisions on grids drawn from {{48,64,80,96}}^3, "
+                  "R=L/6, W=4, density ratio 10, Weber log-uniform in [1,100] via speed, b ~ U[0,1]*2R")
+
+
+def run_sweep(args, world, rank, local):
+    """The batched sweep: every case advanced through one CUDA graph per two steps (lbm_batch_step),
+    against the same cases advanced by per-case lbm_step calls, one case after another."""
+    import numpy as np
+    import torch
+
+    from paper_2603_17481_gb300 import binding as B
+    from paper_2603_17481_gb300 import build as lbm_build
+    from paper_2603_17481_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    lbm_build.build()
+    cfgs = W.c4_sweep(args.cases, seed=17481 + rank)
+    stream = torch.cuda.Stream()
+    sims, m0 = [], []
+    for cfg in cfgs:
+        phi, u = W.c4_fields(cfg)
+        s = B.Lbm(cfg, stream=stream.cuda_stream)
+        s.init_fields(phi, u)
+        m0.append(s.mass()[0])
+        sims.append(s)
+    cells = sum(s.N for s in sims)
+    kernels_per_step = sum(4 if c["nci_on"] else 2 for c in cfgs)
+    steps = args.steps + (args.steps & 1)  # whole graph launches
+
+    def timed(run, k):
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run(k)
+        e1.record(stream)
+        e1.synchronize()
+        barrier(world)
+        return e0.elapsed_time(e1)
+
+    def per_case(k):
+        for s in sims:
+            s.step(k)
+
+    per_case(args.warmup)
+    ms_single = timed(per_case, steps)
+    mlups_single, ms_single_max = whole_job_mlups(world, cells, steps, ms_single, device=f"cuda:{local}")
+
+    results = {}
+    sampler = ClockSampler(local)
+    for ns in args.streams:
+        batch = B.LbmBatch(sims, nstreams=ns, stream=stream.cuda_stream)
+        batch.step(args.warmup + (args.warmup & 1), sync=True)
+        if ns == args.streams[-1]:
+            sampler.start()
+            time.sleep(0.3)
+        ms = timed(lambda k: batch.step(k, sync=False), steps)
+        results[ns] = whole_job_mlups(world, cells, steps, ms, device=f"cuda:{local}")
+        batch.close()
+    clocks = sampler.stop()
+    best = max(results, key=lambda ns: results[ns][0])
+    mlups, ms_max = results[best]
+
+    drift, nonfinite = 0.0, 0
+    for s, m in zip(sims, m0):
+        m1, _ = s.mass()
+        if not np.isfinite(m1):
+            nonfinite += 1
+        else:
+            drift = max(drift, abs(m1 - m) / abs(m))
+    for s in sims:
+        s.close()
+    if rank != 0:
+        return None
+    peak, peak_kind = measured_peaks()
+    frac = mlups / world * 1e6 * step_bytes_per_cell(19, 4) / (peak * 1e9)
+    return {
+        "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": SWEEP_WORKLOAD.format(n=len(cfgs)), "cases": len(cfgs), "cells": cells,
+                   "graph_branches": best, "l2": "inputs larger than L2 (%.1f GB of populations), no flush"
+                   % (2 * 19 * 4 * cells / 1e9),
+                   "parallelism": f"{world} independent replica(s), one per GPU"},
+        "per_case_launches": {"value": round(mlups_single, 1), "unit": "MLUPS",
+                              "ms_per_step": round(ms_single_max / steps, 5),
+                              "what": "lbm_step(K) per case, cases one after another on one stream"},
+        "batched_vs_per_case": round(mlups / mlups_single, 3),
+        "by_graph_branches": {str(ns): round(v[0], 1) for ns, v in results.items()},
+        "step_roofline": {"bytes_per_cell": step_bytes_per_cell(19, 4), "frac_of_measured": round(frac, 4),
+                          "peak": peak, "peak_source": peak_kind},
+        "gpu_launches": kernels_per_step * steps,
+        "clocks": clocks,
+        "phi_mass_drift_max": drift, "nonfinite_cases": nonfinite,
+    }
+
+
 def run_reference(args, world, rank):
     """The FP64 CPU oracle as the reference arm, each step a bounded crop of the same workload."""
     if rank != 0:
@@ -389,10 +486,16 @@ def main():
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=120.0, help="seconds for the whole reference arm")
+    ap.add_argument("--workload", choices=["collision", "sweep"], default="collision",
+                    help="collision: the 256x128x128 head-on case; sweep: the batched sweep of independent cases")
+    ap.add_argument("--cases", type=int, default=512, help="sweep: number of cases")
+    ap.add_argument("--streams", type=int, nargs="+", default=[16], help="sweep: graph branch counts to time")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         line = run_reference(args, world, rank)
+    elif args.workload == "sweep":
+        line = run_sweep(args, world, rank, local)
     else:
         line = run_ours(args, world, rank, local)
     if rank == 0 and line is not None:

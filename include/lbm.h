@@ -141,6 +141,27 @@ int lbm_mass_noalloc(lbm_ctx *ctx, double *phi_mass, double *mom);
  * chi = 0) and the repulsive force density F_rep (3N). Either pointer may be NULL. */
 int lbm_read_nci(lbm_ctx *ctx, int32_t *partner, double *frep);
 
+/* Batches: independent contexts advanced together (a parameter sweep of uneven cases; no
+ * counterpart in the paper, which runs one case at a time). One CUDA graph holds two steps of
+ * every context, the contexts spread over nstreams concurrent branches, so that small cases fill
+ * the GPU together and each kernel launch is paid once per graph rather than once per call.
+ * ctxs: n distinct contexts, initialised, on the current device, with mass_check_every = 0 and
+ * the profiler off (else LBM_ERR_ARG; uninitialised: LBM_ERR_STATE). They stay owned by the caller
+ * and must outlive the batch; while the batch exists only lbm_batch_step may advance them (reads
+ * and lbm_mass on their own streams remain allowed once lbm_batch_step's work is complete).
+ * stream: the cudaStream_t the graph is launched on (NULL: a stream of the batch's own).
+ * *out receives the batch; on error nothing is allocated. */
+typedef struct lbm_batch lbm_batch;
+int lbm_batch_create(lbm_ctx *const *ctxs, int n, int nstreams, void *stream, lbm_batch **out);
+/* Advances every context by nsteps: one graph launch per two steps, and for an odd nsteps a last
+ * plain step of each context, all on the batch's launch stream. Asynchronous like lbm_step:
+ * synchronise the launch stream (or call lbm_batch_synchronize) before reading results. */
+int lbm_batch_step(lbm_batch *b, int nsteps);
+/* Waits for the batch's launch stream. */
+int lbm_batch_synchronize(lbm_batch *b);
+/* Waits for the batch's work, then frees the graph and the batch's streams (not the contexts). */
+void lbm_batch_destroy(lbm_batch *b);
+
 /* Waits for all work of ctx. */
 int lbm_synchronize(lbm_ctx *ctx);
 

@@ -72,6 +72,11 @@ def load():
     L.lbm_mass.argtypes = [_VP, _VP, _VP]
     L.lbm_read_nci.argtypes = [_VP, _VP, _VP]
     L.lbm_mass_noalloc.argtypes = [_VP, _VP, _VP]
+    L.lbm_batch_create.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.POINTER(_VP)]
+    L.lbm_batch_step.argtypes = [_VP, ctypes.c_int]
+    L.lbm_batch_synchronize.argtypes = [_VP]
+    L.lbm_batch_destroy.argtypes = [_VP]
+    L.lbm_batch_destroy.restype = None
     L.lbm_synchronize.argtypes = [_VP]
     L.lbm_profile.argtypes = [_VP, ctypes.c_int]
     L.lbm_profile_read.argtypes = [_VP, _VP, _VP]
@@ -82,7 +87,8 @@ def load():
     L.lbm_kernel_name.restype = ctypes.c_char_p
     for name in ("lbm_create", "lbm_set_stream", "lbm_init_fields", "lbm_set_state", "lbm_get_state",
                  "lbm_step", "lbm_read_fields", "lbm_mass", "lbm_mass_noalloc", "lbm_read_nci", "lbm_synchronize",
-                 "lbm_profile", "lbm_profile_read", "lbm_lattice"):
+                 "lbm_profile", "lbm_profile_read", "lbm_lattice", "lbm_batch_create", "lbm_batch_step",
+                 "lbm_batch_synchronize"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -236,6 +242,56 @@ def lbm_lattice(dim: int, Q: int):
     w = np.zeros(Q)
     _check(load().lbm_lattice(int(dim), int(Q), c.ctypes.data, w.ctypes.data), "lbm_lattice")
     return c, w
+
+
+def lbm_batch_create(ctxs, nstreams: int = 8, stream: int = 0) -> int:
+    arr = (_VP * len(ctxs))(*[_VP(c) for c in ctxs])
+    h = _VP()
+    _check(load().lbm_batch_create(arr, len(ctxs), int(nstreams), _VP(stream or None), ctypes.byref(h)),
+           "lbm_batch_create")
+    return h.value
+
+
+def lbm_batch_step(batch: int, n: int) -> None:
+    _check(load().lbm_batch_step(_VP(batch), int(n)), "lbm_batch_step")
+
+
+def lbm_batch_synchronize(batch: int) -> None:
+    _check(load().lbm_batch_synchronize(_VP(batch)), "lbm_batch_synchronize")
+
+
+def lbm_batch_destroy(batch: int) -> None:
+    if batch:
+        load().lbm_batch_destroy(_VP(batch))
+
+
+class LbmBatch:
+    """Independent contexts advanced together through one CUDA graph (keeps the contexts alive)."""
+
+    def __init__(self, sims, nstreams: int = 8, stream: int = 0):
+        self.sims = list(sims)
+        self.h = lbm_batch_create([s.ctx for s in self.sims], nstreams, stream)
+
+    def step(self, n: int = 2, sync: bool = True):
+        """Advances every context by n steps; with ``sync`` waits for the work (so that the
+        contexts' own reads may follow)."""
+        lbm_batch_step(self.h, n)
+        if sync:
+            lbm_batch_synchronize(self.h)
+
+    def synchronize(self):
+        lbm_batch_synchronize(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Lbm:

@@ -489,15 +489,21 @@ static cudaError_t launch_phase_dim(const KParams &P, const int32_t *phi, const 
   return cudaGetLastError();
 }
 
+// Raises k_phase3's dynamic shared-memory limit once. Context creation calls this, so that the
+// launches themselves make no non-stream CUDA call (they may be captured into a graph).
+cudaError_t phase_prepare(int dim) {
+  static bool attr = false;
+  if (dim != 3 || attr) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(k_phase3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Phase3::smem);
+  if (e == cudaSuccess) attr = true;
+  return e;
+}
+
 static cudaError_t launch_phase3(const KParams &P, const int32_t *phi, const float *u, int32_t *phi_out, int *tiles,
                                  int *ntiles, cudaStream_t s) {
   using G = Phase3;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_phase3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  const cudaError_t e = phase_prepare(3);
+  if (e != cudaSuccess) return e;
   dim3 grid((P.nx + G::TX - 1) / G::TX, (P.ny + G::TY - 1) / G::TY, (P.nz + G::ZC - 1) / G::ZC);
   k_phase3<<<grid, dim3(32, G::TY), G::smem, s>>>(P, phi, u, phi_out, tiles, ntiles);
   return cudaGetLastError();

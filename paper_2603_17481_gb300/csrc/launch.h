@@ -21,6 +21,7 @@ cudaError_t launch_nci(int dim, const KParams &P, const NciTable &T, const int32
                        int32_t *partner, int debug, const int *tiles, const int *ntiles, int list_blocks,
                        cudaStream_t s);
 int nci_list_blocks(int dim);
+cudaError_t phase_prepare(int dim);
 
 // src/dst are population buffers of the store type; MODE kStep writes dst and u, kMoments writes
 // u and pstar only.

@@ -237,6 +237,7 @@ int lbm_create(const lbm_params *p, lbm_ctx **out) {
     c->nci_blocks = nci_list_blocks(p->dim);
     if (c->nci_blocks <= 0) e = cudaErrorInvalidConfiguration;
   }
+  if (e == cudaSuccess) e = phase_prepare(p->dim);
   if (e == cudaSuccess) e = cudaMalloc(&c->red_part, sizeof(ReduceOut) * kReduceBlocks);
   if (e == cudaSuccess) e = cudaMalloc(&c->red_out, sizeof(ReduceOut));
   if (e == cudaSuccess) e = cudaMemset(c->u, 0, sizeof(float) * 3 * c->N);

@@ -114,6 +114,45 @@ def c3_head_on_3d(nx=256, ny=128, nz=128, R=24.0, Q=19):
     return cfg, phi, u
 
 
+#: Grid edges of the batched collision sweep (cubic periodic boxes).
+SWEEP_GRIDS = (48, 64, 80, 96)
+
+
+def c4_sweep(n=512, seed=17481, u_max=0.1, we_min=1.0, we_max=100.0, grids=SWEEP_GRIDS):
+    """Parameter sets of the batched sweep: ``n`` independent 3D D3Q19 collisions, density ratio 10.
+
+    Each case draws its cubic grid edge L from ``grids``, R = L / 6, a Weber number
+    We = rho_l U^2 (2R) / sigma log-uniform in [we_min, we_max] and an impact offset b ~ U(0, 1) 2R
+    along y. The Weber number is set through the speed: sigma = rho_l u_max^2 (2R) / we_max, so that
+    the relative speed U = u_max sqrt(We / we_max) stays within [u_max / 10, u_max] in lattice
+    units; A_rep = sigma. The droplets start 2R + 8 apart along x, moving at -+U/2.
+    Fields come from ``c4_fields``.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        L = int(grids[int(rng.integers(0, len(grids)))])
+        R = L / 6.0
+        we = float(math.exp(rng.uniform(math.log(we_min), math.log(we_max))))
+        b = float(rng.uniform(0.0, 1.0)) * 2.0 * R
+        sigma = 1.0 * u_max * u_max * 2.0 * R / we_max
+        U = u_max * math.sqrt(we / we_max)
+        cfg = base_config(3, L, L, L, 19, rho_g=0.1, sigma=sigma, A_rep=sigma, steps=1000)
+        c = (L - 1) / 2.0
+        sep = 2 * R + 8
+        cfg.update(case=i, R=R, weber=we, impact_offset=b, speed=U,
+                   centers=[(c - sep / 2, c - b / 2, c), (c + sep / 2, c + b / 2, c)],
+                   velocities=[(U / 2, 0.0, 0.0), (-U / 2, 0.0, 0.0)])
+        out.append(cfg)
+    return out
+
+
+def c4_fields(cfg):
+    """phi (rounded to the 2^-30 grid) and u of one sweep case."""
+    phi, u = droplet_fields(cfg, cfg["centers"], [cfg["R"], cfg["R"]], cfg["velocities"])
+    return to_q30_grid(phi), u
+
+
 def swarm_centres(L, nb, rmin, rmax, eps, seed=17481, max_tries=2_000_000):
     """Rejection-sampled non-overlapping bubbles in a periodic cube: centre distance >= R_i + R_j + eps."""
     rng = np.random.default_rng(seed)

@@ -1,0 +1,115 @@
+"""Batched sweep: contexts advanced together through one CUDA graph give exactly the states that
+per-case lbm_step calls give, and a sweep case follows the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2603_17481_gb300 import binding as B
+from paper_2603_17481_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2603_17481_gb300 import build
+    build.build()
+    O.build()
+    torch.cuda.set_device(0)
+    return True
+
+
+def _small_cases():
+    """Uneven small cases, 2D and 3D, both stencil families, near-contact on and off."""
+    cases = []
+    for i, L in enumerate((24, 40, 32, 20, 36)):
+        cfg = W.c4_sweep(1, seed=100 + i, grids=(L,))[0]
+        if i == 3:
+            cfg["nci_on"] = 0
+        cases.append(cfg)
+    c2 = W.base_config(2, 70, 38, 1, 9, rho_g=0.1)
+    c2.update(centers=[(24.0, 19.3, 0.0), (45.5, 18.6, 0.0)], R=8.0,
+              velocities=[(0.02, 0.0, 0.0), (-0.02, 0.0, 0.0)])
+    cases.append(c2)
+    c27 = W.c4_sweep(1, seed=7, grids=(28,))[0]
+    c27["Q"] = 27
+    cases.append(c27)
+    return cases
+
+
+def _states(sims):
+    return [s.get_state() for s in sims]
+
+
+@pytest.mark.parametrize("nstreams", [1, 3, 16])
+def test_batch_matches_per_case_steps(nstreams):
+    cases = _small_cases()
+    single, batched = [], []
+    for cfg in cases:
+        phi, u = W.c4_fields(cfg)
+        for lst in (single, batched):
+            s = B.Lbm(cfg)
+            s.init_fields(phi, u)
+            lst.append(s)
+    batch = B.LbmBatch(batched, nstreams=nstreams)
+    for n in (4, 3, 0, 1):  # even (graph only), odd (graph + one plain step), none, plain only
+        batch.step(n)
+        for s in single:
+            s.step(n)
+        for a, b in zip(_states(single), _states(batched)):
+            assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    for a, b in zip(single, batched):
+        ma, pa = a.mass()
+        mb, pb = b.mass()
+        assert ma == mb and np.array_equal(pa, pb)
+    batch.close()
+    for s in single + batched:
+        s.close()
+
+
+def test_batch_case_against_oracle():
+    """A 40^3 sweep case advanced 20 steps inside a batch of three against the FP64 oracle."""
+    cfgs = [W.c4_sweep(1, seed=s, grids=(L,))[0] for s, L in ((3, 40), (4, 24), (5, 32))]
+    sims = []
+    for cfg in cfgs:
+        phi, u = W.c4_fields(cfg)
+        s = B.Lbm(cfg)
+        s.init_fields(phi, u)
+        sims.append(s)
+    batch = B.LbmBatch(sims, nstreams=2)
+    batch.step(20)
+    cfg = cfgs[0]
+    phi, u = W.c4_fields(cfg)
+    P = O.make_params(cfg)
+    f = O.init(P, phi, u)
+    fo, pho, _ = O.step(P, f, phi, 20)
+    _, uo = O.moments(P, fo, pho)
+    phg, ug, _ = sims[0].read_fields()
+    assert np.max(np.abs(phg - pho)) <= 1e-5
+    assert np.max(np.abs(ug - uo)) <= 1e-6
+    batch.close()
+    for s in sims:
+        s.close()
+
+
+def test_batch_rejects_bad_contexts():
+    cfg = W.c4_sweep(1, seed=1, grids=(20,))[0]
+    phi, u = W.c4_fields(cfg)
+    checked = B.Lbm(cfg, mass_check_every=10)
+    checked.init_fields(phi, u)
+    fresh = B.Lbm(cfg)  # never initialised
+    ok = B.Lbm(cfg)
+    ok.init_fields(phi, u)
+    with pytest.raises(B.LbmError) as e:
+        B.LbmBatch([ok, checked])
+    assert e.value.code == -1
+    with pytest.raises(B.LbmError) as e:
+        B.LbmBatch([ok, fresh])
+    assert e.value.code == -5
+    with pytest.raises(B.LbmError) as e:
+        B.LbmBatch([ok, ok])
+    assert e.value.code == -1
+    for s in (checked, fresh, ok):
+        s.close()
