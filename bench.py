@@ -421,6 +421,103 @@ def run_sweep(args, world, rank, local):
     }
 
 
+SWARM_WORKLOAD = ("3D buoyant bubble swarm, 512^3 periodic D3Q19, {nb} bubbles R ~ U[8,12] at seeded "
+                  "non-overlapping positions (gas fraction {gf:.3f}), W=4, density ratio 100, g=1e-6")
+
+
+def count_bubbles(gas):
+    """Connected components (6-neighbour) of a boolean (nz, ny, nx) mask on a periodic grid."""
+    from scipy import ndimage
+    lab, n = ndimage.label(gas)
+    parent = list(range(n + 1))
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+
+    for ax in range(3):
+        a = lab.take(0, axis=ax).ravel()
+        b = lab.take(-1, axis=ax).ravel()
+        m = (a > 0) & (b > 0)
+        for i, j in set(zip(a[m].tolist(), b[m].tolist())):
+            ri, rj = find(i), find(j)
+            if ri != rj:
+                parent[max(ri, rj)] = min(ri, rj)
+    return len({find(i) for i in range(1, n + 1)})
+
+
+def run_swarm(args, world, rank, local):
+    """The bubble swarm with the near-contact repulsion on and off: throughput of each, and the
+    number of distinct bubbles (gas components) left after --swarm-steps steps."""
+    import numpy as np
+    import torch
+
+    from paper_2603_17481_gb300 import binding as B
+    from paper_2603_17481_gb300 import build as lbm_build
+    from paper_2603_17481_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    lbm_build.build()
+    cfg, cs, rs = W.c5_swarm(L=args.swarm_L, nb=args.swarm_bubbles, seed=17481 + rank)
+    phi, u = W.c5_fields(cfg, cs, rs)
+    N = W.ncells(cfg)
+    L = cfg["nx"]
+    nb0 = count_bubbles((phi < 0.5).reshape(L, L, L))
+    stream = torch.cuda.Stream()
+    runs = {}
+    for name, nci, store in (("nci_on", 1, "f32"), ("nci_off", 0, "f32"), ("nci_on_f16", 1, "f16")):
+        c = dict(cfg, nci_on=nci)
+        sim = B.Lbm(c, store=store, stream=stream.cuda_stream)
+        sim.init_fields(phi, u)
+        m0, _ = sim.mass()
+        sim.step(args.warmup)
+        sim.synchronize()
+        sim.profile(True)
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            sim.step(1)
+        e1.record(stream)
+        e1.synchronize()
+        barrier(world)
+        prof = sim.profile_read()
+        sim.profile(False)
+        mlups, ms_max = whole_job_mlups(world, N, args.steps, e0.elapsed_time(e1), device=f"cuda:{local}")
+        rest = args.swarm_steps - args.warmup - args.steps
+        if rest > 0:
+            sim.step(rest)
+        ph, _, _ = sim.read_fields(want=("phi",))
+        m1, _ = sim.mass()
+        runs[name] = {"value": round(mlups, 1), "ms_per_step": round(ms_max / args.steps, 5),
+                      "kernels_ms_per_step": {k: round(ms / max(n, 1), 5) for k, (ms, n) in prof.items() if n},
+                      "bubbles_after": count_bubbles((ph < 0.5).reshape(L, L, L)) if np.all(np.isfinite(ph)) else None,
+                      "after_steps": max(args.swarm_steps, args.warmup + args.steps),
+                      "phi_mass_drift": abs(m1 - m0) / abs(m0)}
+        sim.close()
+    if rank != 0:
+        return None
+    peak, peak_kind = measured_peaks()
+    on = runs["nci_on"]["value"]
+    return {
+        "metric": METRIC, "value": on, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": runs["nci_on"]["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": SWARM_WORKLOAD.format(nb=len(cs), gf=float((phi < 0.5).mean())), "cells": N,
+                   "l2": "inputs larger than L2, no flush",
+                   "parallelism": f"{world} independent replica(s), one per GPU"},
+        "step_roofline": {"bytes_per_cell": step_bytes_per_cell(19, 4),
+                          "frac_of_measured": round(on / world * 1e6 * step_bytes_per_cell(19, 4) / (peak * 1e9), 4),
+                          "peak": peak, "peak_source": peak_kind},
+        "nci_overhead": round(runs["nci_off"]["value"] / on - 1.0, 4),
+        "bubbles_initial": nb0, "runs": runs,
+        "gpu_launches": int(4 * args.steps),
+    }
+
+
 def run_reference(args, world, rank):
     """The FP64 CPU oracle as the reference arm, each step a bounded crop of the same workload."""
     if rank != 0:
@@ -486,16 +583,22 @@ def main():
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=120.0, help="seconds for the whole reference arm")
-    ap.add_argument("--workload", choices=["collision", "sweep"], default="collision",
-                    help="collision: the 256x128x128 head-on case; sweep: the batched sweep of independent cases")
+    ap.add_argument("--workload", choices=["collision", "sweep", "swarm"], default="collision",
+                    help="collision: the 256x128x128 head-on case; sweep: the batched sweep of independent "
+                         "cases; swarm: the 512^3 bubble swarm with the near-contact repulsion on and off")
     ap.add_argument("--cases", type=int, default=512, help="sweep: number of cases")
     ap.add_argument("--streams", type=int, nargs="+", default=[16], help="sweep: graph branch counts to time")
+    ap.add_argument("--swarm-L", type=int, default=512)
+    ap.add_argument("--swarm-bubbles", type=int, default=1500)
+    ap.add_argument("--swarm-steps", type=int, default=0, help="swarm: total steps before counting bubbles")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         line = run_reference(args, world, rank)
     elif args.workload == "sweep":
         line = run_sweep(args, world, rank, local)
+    elif args.workload == "swarm":
+        line = run_swarm(args, world, rank, local)
     else:
         line = run_ours(args, world, rank, local)
     if rank == 0 and line is not None:

@@ -224,7 +224,8 @@ k_phase(const KParams P, const int32_t *__restrict__ phi, const float *__restric
 }
 
 // ---------------------------------------------------------------------------------------------
-// 3D: a block owns a 32 x 8 column of cells over ZC planes and marches along z, keeping ring
+// 3D: a block owns a 32 x 8 column of cells over zc planes (zc = 16, or 8 or 4 on grids too small
+// to fill the GPU with 16-plane columns) and marches along z, keeping ring
 // buffers of planes in shared memory. The D3Q27 weights factor as s(c_x) s(c_y) s(c_z) / 216, so
 //   RZ(k)   = phi(k-1) + 4 phi(k) + phi(k+1)         (exact, 64-bit)
 //   PSXY(k) = s_x s_y phi(k)                         (exact, 64-bit)
@@ -237,7 +238,7 @@ k_phase(const KParams P, const int32_t *__restrict__ phi, const float *__restric
 // are computed by both neighbours from identical inputs with the same rounded operations.
 // ---------------------------------------------------------------------------------------------
 struct Phase3 {
-  static constexpr int TX = 32, TY = 8, ZC = 16, NT = TX * TY;
+  static constexpr int TX = 32, TY = 8, ZC = 16, NT = TX * TY;  // ZC: the largest z chunk
   static constexpr int PX = TX + 4, PY = TY + 4, NP = PX * PY;  // phi / RZ planes (halo 2)
   static constexpr int QX = TX + 2, QY = TY + 2, NQ = QX * QY;  // PSXY / a planes (halo 1)
   static constexpr int NC = TX * TY;
@@ -254,7 +255,7 @@ __device__ __forceinline__ long long s141(long long a, long long b, long long c)
 
 __global__ void __launch_bounds__(Phase3::NT, 4)
 k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restrict__ u,
-         int32_t *__restrict__ phi_out, int *__restrict__ tiles, int *__restrict__ ntiles) {
+         int32_t *__restrict__ phi_out, int *__restrict__ tiles, int *__restrict__ ntiles, const int zc) {
   using G = Phase3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   long long *RZ = reinterpret_cast<long long *>(smem_raw);  // [2][NP]
@@ -276,7 +277,7 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
   const int nx = P.nx, ny = P.ny, nz = P.nz;
   const long long N = P.N;
   const int x0 = blockIdx.x * G::TX, y0 = blockIdx.y * G::TY;
-  const int zb = blockIdx.z * G::ZC, ze = min(zb + G::ZC, nz);
+  const int zb = blockIdx.z * zc, ze = min(zb + zc, nz);
   const float D = P.Dlap * (1.0f / 6.0f);
   const float k3 = P.kc * kCs2 * 3.0f;  // 3 kappa
   // this thread's x columns for plane loads: phi planes (lx = lane - 2, and 30..33 for lanes 0..3),
@@ -491,12 +492,31 @@ static cudaError_t launch_phase_dim(const KParams &P, const int32_t *phi, const 
 
 // Raises k_phase3's dynamic shared-memory limit once. Context creation calls this, so that the
 // launches themselves make no non-stream CUDA call (they may be captured into a graph).
+// It also records how many k_phase3 blocks the device holds at once (SMs x resident blocks).
+static int g_phase3_slots = 0;
+
 cudaError_t phase_prepare(int dim) {
   static bool attr = false;
   if (dim != 3 || attr) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(k_phase3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Phase3::smem);
-  if (e == cudaSuccess) attr = true;
+  cudaError_t e = cudaFuncSetAttribute(k_phase3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Phase3::smem);
+  int dev = 0, sms = 0, per = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_phase3, Phase3::NT, Phase3::smem);
+  if (e == cudaSuccess) {
+    g_phase3_slots = sms * (per > 0 ? per : 1);
+    attr = true;
+  }
   return e;
+}
+
+// z chunk of a k_phase3 launch: 16 planes (4 of them re-read as the march's prologue), halved
+// while the grid of columns would not fill the device once.
+int phase3_zc(int nx, int ny, int nz) {
+  const long long cols = (long long)((nx + Phase3::TX - 1) / Phase3::TX) * ((ny + Phase3::TY - 1) / Phase3::TY);
+  int zc = Phase3::ZC;
+  while (zc > 4 && cols * ((nz + zc - 1) / zc) < g_phase3_slots) zc /= 2;
+  return zc;
 }
 
 static cudaError_t launch_phase3(const KParams &P, const int32_t *phi, const float *u, int32_t *phi_out, int *tiles,
@@ -504,8 +524,9 @@ static cudaError_t launch_phase3(const KParams &P, const int32_t *phi, const flo
   using G = Phase3;
   const cudaError_t e = phase_prepare(3);
   if (e != cudaSuccess) return e;
-  dim3 grid((P.nx + G::TX - 1) / G::TX, (P.ny + G::TY - 1) / G::TY, (P.nz + G::ZC - 1) / G::ZC);
-  k_phase3<<<grid, dim3(32, G::TY), G::smem, s>>>(P, phi, u, phi_out, tiles, ntiles);
+  const int zc = phase3_zc(P.nx, P.ny, P.nz);
+  dim3 grid((P.nx + G::TX - 1) / G::TX, (P.ny + G::TY - 1) / G::TY, (P.nz + zc - 1) / zc);
+  k_phase3<<<grid, dim3(32, G::TY), G::smem, s>>>(P, phi, u, phi_out, tiles, ntiles, zc);
   return cudaGetLastError();
 }
 

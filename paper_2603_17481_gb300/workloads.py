@@ -183,6 +183,32 @@ def c5_swarm(L=512, nb=1500, seed=17481, rmin=8.0, rmax=12.0):
     return cfg, cs, rs
 
 
+def c5_fields(cfg, cs, rs, cut=4.0):
+    """phi of the bubble swarm (gas inside, phi = 0), u = 0, built box by box.
+
+    Each bubble's profile (1 + tanh(2 (R - r) / eps)) / 2 is evaluated only within a cube of half
+    width R + cut * eps around its centre (beyond it the profile is below 1.2e-7 for cut = 4 and is
+    taken as 0); phi = max(0, 1 - sum of profiles), rounded to the 2^-30 grid. Returns phi (N,)
+    and u (3, N) in x-fastest order.
+    """
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    eps = cfg["eps"]
+    acc = np.zeros((nz, ny, nx))
+    for c, R in zip(cs, rs):
+        h = int(math.ceil(R + cut * eps))
+        lo = [int(math.floor(c[a])) - h for a in range(3)]
+        ix = np.arange(lo[0], lo[0] + 2 * h + 2)
+        iy = np.arange(lo[1], lo[1] + 2 * h + 2)
+        iz = np.arange(lo[2], lo[2] + 2 * h + 2)
+        dx, dy, dz = ix - c[0], iy - c[1], iz - c[2]
+        r = np.sqrt(dz[:, None, None] ** 2 + dy[None, :, None] ** 2 + dx[None, None, :] ** 2)
+        prof = 0.5 * (1.0 + np.tanh(2.0 * (R - r) / eps))
+        prof[r > R + cut * eps] = 0.0
+        acc[np.ix_(iz % nz, iy % ny, ix % nx)] += prof
+    phi = np.maximum(0.0, 1.0 - acc).reshape(-1)
+    return to_q30_grid(phi), np.zeros((3, phi.size))
+
+
 def smooth_random_fields(cfg, seed, n_modes=4, amp_u=0.03, pairs=True):
     """Random smooth periodic phi in (0, 1) with sharp-ish interfaces plus a smooth random u.
 

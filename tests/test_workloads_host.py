@@ -1,0 +1,64 @@
+"""Host-side logic of the workloads and the benchmark: the sweep's parameter ranges, the box-local
+swarm generator against the all-cells generator, and the periodic bubble counter."""
+import math
+import os
+import sys
+
+import numpy as np
+
+from paper_2603_17481_gb300 import workloads as W
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def test_sweep_parameters():
+    cases = W.c4_sweep(512)
+    assert len(cases) == 512
+    assert {c["nx"] for c in cases} == set(W.SWEEP_GRIDS)
+    for c in cases:
+        L, R = c["nx"], c["R"]
+        assert c["ny"] == c["nz"] == L and R == L / 6
+        assert 1.0 <= c["weber"] <= 100.0 and 0.0 <= c["impact_offset"] <= 2 * R
+        # We = rho_l U^2 (2R) / sigma is the drawn Weber number
+        assert math.isclose(c["rho_l"] * c["speed"] ** 2 * 2 * R / c["sigma"], c["weber"], rel_tol=1e-12)
+        assert 0.01 <= c["speed"] <= 0.1
+        (x0, y0, _), (x1, y1, _) = c["centers"]
+        assert math.isclose(x1 - x0, 2 * R + 8) and math.isclose(y1 - y0, c["impact_offset"])
+    # reproducible from the seed
+    assert W.c4_sweep(3, seed=5) == W.c4_sweep(3, seed=5)
+
+
+def test_swarm_fields_match_all_cells_profile():
+    cfg, cs, rs = W.c5_swarm(L=64, nb=12, seed=4)
+    assert len(cs) == 12
+    for i in range(len(cs)):
+        for j in range(i):
+            d = cs[i] - cs[j]
+            d -= 64 * np.round(d / 64)
+            assert np.linalg.norm(d) >= rs[i] + rs[j] + cfg["eps"]
+    phi, u = W.c5_fields(cfg, cs, rs)
+    ref, _ = W.droplet_fields(cfg, cs, rs, [(0, 0, 0)] * len(cs), bubbles=True)
+    # each truncated profile tail is below 1.2e-7, so the fields differ by less than that per bubble
+    assert np.max(np.abs(phi - ref)) < 1.2e-7 * len(cs)
+    assert not np.any(u)
+
+
+def test_count_bubbles_periodic():
+    g = np.zeros((8, 8, 8), bool)
+    g[0, 0, 0] = g[7, 0, 0] = True  # joined across z
+    g[3, 3, 3] = True
+    g[0, 5, 0] = g[0, 5, 7] = True  # joined across x
+    g[2, 0, 4] = g[2, 7, 4] = True  # joined across y
+    assert bench.count_bubbles(g) == 4
+    g[3, 3, 4] = True  # touches (3,3,3)
+    assert bench.count_bubbles(g) == 4
+    g[5, 5, 5] = True
+    assert bench.count_bubbles(g) == 5
+    assert bench.count_bubbles(np.zeros((4, 4, 4), bool)) == 0
+
+
+def test_count_bubbles_of_generated_swarm():
+    cfg, cs, rs = W.c5_swarm(L=96, nb=20, seed=9)
+    phi, _ = W.c5_fields(cfg, cs, rs)
+    assert bench.count_bubbles((phi < 0.5).reshape(96, 96, 96)) == len(cs)
