@@ -44,7 +44,10 @@ def hydro_bytes_per_cell(Q, pop_bytes):
 # DRAM traffic of one hydrodynamic launch on the full workload, from the ncu capture summarised in
 # profiles/ (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hydro kernel source hash:
 # a changed kernel reports null until it is profiled again.
-HYDRO_TRAFFIC = {}
+HYDRO_TRAFFIC = {
+    # 337.48 MB read + 322.91 MB written (ncu --set full, one step launch of the 256x128x128 case)
+    ("f32", "3a4e6e5724843be3"): 660.38e6,
+}
 
 
 def _src_hash(*names):
@@ -216,6 +219,9 @@ def run_ours(args, world, rank, local):
     ms_total = ev0.elapsed_time(ev1)
     mlups, ms_max = whole_job_mlups(world, N, args.steps, ms_total, device=f"cuda:{local}")
     m1, _ = sim.mass()
+    n32 = args.warmup + args.steps
+    want_variants = args.variants and args.store == "f32" and world == 1
+    ph32 = sim.read_fields(want=("phi",))[0] if want_variants else None  # phi after n32 steps
 
     pop_b = 4 if args.store == "f32" else 2
     peak, peak_kind = measured_peaks()
@@ -255,8 +261,7 @@ def run_ours(args, world, rank, local):
                "steps": ke, "what": "lbm_init_fields(pinned host) + steps x lbm_step(1) + lbm_read_fields(pinned host)"}
 
     variants = {}
-    if args.variants and args.store == "f32" and world == 1:
-        ph32, _, _ = sim.read_fields(want=("phi",))
+    if want_variants:
         for st in ("f16", "bf16"):
             s2 = B.Lbm(cfg, store=st, stream=stream.cuda_stream)
             s2.init_fields(phi, u)
@@ -276,14 +281,14 @@ def run_ours(args, world, rank, local):
             v_mlups = N * kv / (msv * 1e-3) / 1e6
             # phi after the same number of steps as the FP32 run, compared with it
             s2.init_fields(phi, u)
-            s2.step(args.warmup + args.steps)
+            s2.step(n32)
             ph2, _, _ = s2.read_fields(want=("phi",))
             variants[st] = {
                 "value": round(v_mlups, 1), "steps": kv,
                 "hydro_gbs": round(hydro_bytes_per_cell(Q, 2) * N / (hm / hn * 1e-3) / 1e9, 1),
                 "step_roofline_frac": round(v_mlups * 1e6 * step_bytes_per_cell(Q, 2) / (peak * 1e9), 4),
-                "max_abs_phi_diff_vs_f32_after_%d_steps" % (args.warmup + args.steps):
-                    float(np.max(np.abs(ph2 - ph32))),
+                "max_abs_phi_diff_vs_f32_after_%d_steps" % n32: float(np.max(np.abs(ph2 - ph32))),
+                "phi_mass_drift": abs(s2.mass()[0] - m0) / abs(m0),
             }
             s2.close()
 

@@ -9,10 +9,15 @@
 //                  the gated cells of the tile compacted into a list, then one warp per gated cell
 //                  tests 32 window offsets per iteration in (|r|^2, canonical index) order and
 //                  stops after the first shell holding an accepted candidate.
-// Before scanning, each tile bounds n(x).n(y) from below over its whole halo box by the component
-// ranges [lo_a, hi_a] of its gated normals: sum_a min(n_a lo_a, n_a hi_a) <= n(x).n(y). A cell whose
-// bound exceeds the facing threshold cannot have a candidate (Eq. 62) and skips the scan; this is
-// exact (a rounding margin of 1e-5 is kept), and it removes the scan on isolated interfaces.
+// Before scanning, a cell bounds n(x).n(y) from below by the component ranges [lo_a, hi_a] of the
+// gated normals around it: sum_a min(n_a lo_a, n_a hi_a) <= n(x).n(y). A cell whose bound exceeds
+// the facing threshold cannot have a candidate (Eq. 62) and skips the scan; this is exact (a
+// rounding margin of 1e-5 is kept). The ranges are taken first over the whole halo box of the
+// tile, and where that does not decide, over the cell's own 7^3 window: separable sliding min/max
+// filters (z, then y, then x) of the three components, with non-gated cells as NaN (which fminf
+// and fmaxf skip), kept as halves rounded outward (lo down, hi up) so the bound stays a lower
+// bound. A curved interface of radius R turns its normal by about 5/R inside a window, so on
+// isolated drops and bubbles only cells facing another interface within 3 cells are scanned.
 // The force is written only at gated cells; the hydrodynamic kernel reads it exactly there (same
 // gate function).
 #include "launch.h"
@@ -25,9 +30,11 @@ template <int DIM> struct NciGeom {
   static constexpr int HX = TX + 2 * H, HY = TY + 2 * H, HZ = DIM == 3 ? TZ + 2 * H : 1;
   static constexpr int NB = HX * HY * HZ;
   static constexpr int NT = TX * TY * TZ, NW = NT / 32;
+  static constexpr int NZR = HX * HY * TZ;  // z-filtered planes (3D)
+  static constexpr int NYR = HX * TY * TZ;  // z- and y-filtered rows
   static constexpr size_t smem = sizeof(int32_t) * NB + sizeof(float) * 3 * NB + sizeof(int) * (NT + 1) +
                                  sizeof(float) * (6 * (NW + 1) + 1) + sizeof(long long) * (HY * HZ + 1) +
-                                 sizeof(int) * HX;
+                                 sizeof(int) * HX + sizeof(__half) * 6 * ((DIM == 3 ? NZR : 0) + NYR);
 };
 
 template <int DIM>
@@ -90,6 +97,8 @@ k_nci_scan(const KParams P, const NciTable T, const int32_t *__restrict__ phi, c
   float *s_rng = reinterpret_cast<float *>(s_count + 1);  // [NW + 1][6]
   long long *s_row = reinterpret_cast<long long *>(s_rng + 6 * (G::NW + 1) + 1);  // [HY * HZ], 8-aligned
   int *s_col = reinterpret_cast<int *>(s_row + G::HY * G::HZ);                   // [HX]
+  __half *s_yr = reinterpret_cast<__half *>(s_col + G::HX);                        // [6][NYR]
+  __half *s_zr = s_yr + 6 * G::NYR;                                                // [6][NZR] (3D)
 
   const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
   const int tid = tx + G::TX * (ty + G::TY * tz), lane = tid & 31, warp = tid >> 5;
@@ -159,8 +168,11 @@ k_nci_scan(const KParams P, const NciTable T, const int32_t *__restrict__ phi, c
         }
 #pragma unroll
         for (int h = 0; h < BATCH; h++) {
-          if (!gb[h]) continue;
           const int b = t0 + h * G::NT;
+          if (!gb[h]) {
+            if (b < G::NB) s_n[b] = s_n[G::NB + b] = s_n[2 * G::NB + b] = __int_as_float(0x7fffffff);
+            continue;
+          }
           s_n[b] = nb[h].x; s_n[G::NB + b] = nb[h].y; s_n[2 * G::NB + b] = nb[h].z;
           lo0 = fminf(lo0, nb[h].x); lo1 = fminf(lo1, nb[h].y); lo2 = fminf(lo2, nb[h].z);
           hi0 = fmaxf(hi0, nb[h].x); hi1 = fmaxf(hi1, nb[h].y); hi2 = fmaxf(hi2, nb[h].z);
@@ -187,20 +199,93 @@ k_nci_scan(const KParams P, const NciTable T, const int32_t *__restrict__ phi, c
       for (int w = 1; w < G::NW; w++) a = tid < 3 ? fminf(a, s_rng[6 * w + tid]) : fmaxf(a, s_rng[6 * w + tid]);
       s_rng[6 * G::NW + tid] = a;
     }
-    {  // compact the gated cells of the tile
-      const unsigned m = __ballot_sync(0xffffffffu, gated);
+    __syncthreads();
+    const float rlo0 = s_rng[6 * G::NW], rlo1 = s_rng[6 * G::NW + 1], rlo2 = s_rng[6 * G::NW + 2];
+    const float rhi0 = s_rng[6 * G::NW + 3], rhi1 = s_rng[6 * G::NW + 4], rhi2 = s_rng[6 * G::NW + 5];
+    const float thr = P.cos_opp + 1e-5f;
+    const int ob0 = (DIM == 3 ? (tz + G::H) * G::HX * G::HY : 0) + (ty + G::H) * G::HX + tx + G::H;
+    bool scan = false;
+    if (gated) {
+      const float n0 = s_n[ob0], n1 = s_n[G::NB + ob0], n2 = s_n[2 * G::NB + ob0];
+      scan = fminf(n0 * rlo0, n0 * rhi0) + fminf(n1 * rlo1, n1 * rhi1) + fminf(n2 * rlo2, n2 * rhi2) <= thr;
+    }
+    if (__syncthreads_or(scan)) {
+      // window ranges: z pass (3D) over the box columns, y pass, then x per cell
+      if constexpr (DIM == 3) {
+        for (int col = tid; col < G::HX * G::HY; col += G::NT) {
+#pragma unroll
+          for (int a = 0; a < 3; a++) {
+            float v[G::HZ];
+#pragma unroll
+            for (int k = 0; k < G::HZ; k++) v[k] = s_n[a * G::NB + k * G::HX * G::HY + col];
+#pragma unroll
+            for (int o = 0; o < G::TZ; o++) {
+              float lo = v[o], hi = v[o];
+#pragma unroll
+              for (int k = 1; k <= 2 * G::H; k++) { lo = fminf(lo, v[o + k]); hi = fmaxf(hi, v[o + k]); }
+              s_zr[(2 * a) * G::NZR + o * G::HX * G::HY + col] = __float2half_rd(lo);
+              s_zr[(2 * a + 1) * G::NZR + o * G::HX * G::HY + col] = __float2half_ru(hi);
+            }
+          }
+        }
+        __syncthreads();
+      }
+      for (int col = tid; col < G::HX * G::TZ; col += G::NT) {
+        const int cx = col % G::HX, cz = col / G::HX;
+#pragma unroll
+        for (int c = 0; c < 6; c++) {
+          float v[G::HY];
+#pragma unroll
+          for (int k = 0; k < G::HY; k++) {
+            if constexpr (DIM == 3) {
+              v[k] = __half2float(s_zr[c * G::NZR + (cz * G::HY + k) * G::HX + cx]);
+            } else {
+              v[k] = s_n[(c >> 1) * G::NB + k * G::HX + cx];
+            }
+          }
+#pragma unroll
+          for (int o = 0; o < G::TY; o++) {
+            float r = v[o];
+#pragma unroll
+            for (int k = 1; k <= 2 * G::H; k++) r = (c & 1) ? fmaxf(r, v[o + k]) : fminf(r, v[o + k]);
+            s_yr[c * G::NYR + (cz * G::TY + o) * G::HX + cx] = (c & 1) ? __float2half_ru(r) : __float2half_rd(r);
+          }
+        }
+      }
+      __syncthreads();
+      if (scan) {
+        const __half *row = s_yr + (tz * G::TY + ty) * G::HX + tx;
+        float b = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+          float lo = __half2float(row[(2 * a) * G::NYR]), hi = __half2float(row[(2 * a + 1) * G::NYR]);
+#pragma unroll
+          for (int k = 1; k <= 2 * G::H; k++) {
+            lo = fminf(lo, __half2float(row[(2 * a) * G::NYR + k]));
+            hi = fmaxf(hi, __half2float(row[(2 * a + 1) * G::NYR + k]));
+          }
+          const float na = s_n[a * G::NB + ob0];
+          b += fminf(na * lo, na * hi);
+        }
+        scan = b <= thr;
+      }
+    }
+    if (gated && !scan) {  // no candidate can face this cell: no force
+      frep[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (partner) partner[3 * idx] = partner[3 * idx + 1] = partner[3 * idx + 2] = INT32_MIN;
+    }
+    {  // compact the cells to scan
+      const unsigned m = __ballot_sync(0xffffffffu, scan);
       int base = 0;
       if (lane == 0 && m) base = atomicAdd(s_count, __popc(m));
       base = __shfl_sync(0xffffffffu, base, 0);
-      if (gated) s_list[base + __popc(m & ((1u << lane) - 1u))] = tid;
+      if (scan) s_list[base + __popc(m & ((1u << lane) - 1u))] = tid;
     }
     if (debug && inb && !gated) {
       frep[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (partner) partner[3 * idx] = partner[3 * idx + 1] = partner[3 * idx + 2] = INT32_MIN;
     }
     __syncthreads();
-    const float rlo0 = s_rng[6 * G::NW], rlo1 = s_rng[6 * G::NW + 1], rlo2 = s_rng[6 * G::NW + 2];
-    const float rhi0 = s_rng[6 * G::NW + 3], rhi1 = s_rng[6 * G::NW + 4], rhi2 = s_rng[6 * G::NW + 5];
 
     // one warp per gated cell; candidate criteria Eqs. 59, 61, 62; the winner is the nearest
     // accepted candidate, then the largest facing score, then the first in table order (the
@@ -213,9 +298,8 @@ k_nci_scan(const KParams P, const NciTable T, const int32_t *__restrict__ phi, c
       const int32_t vx = s_phi[ob];
       const float qxc = q_gate_value(vx);
       const float n0 = s_n[ob], n1 = s_n[G::NB + ob], n2 = s_n[2 * G::NB + ob];
-      const float bound = fminf(n0 * rlo0, n0 * rhi0) + fminf(n1 * rlo1, n1 * rhi1) + fminf(n2 * rlo2, n2 * rhi2);
       unsigned long long best = ~0ull;
-      if (bound <= P.cos_opp + 1e-5f) {
+      {
         const float sim = __fmul_rn(P.eta, fmaxf(qxc, P.eps_q));
         for (int j0 = 0; j0 < T.count; j0 += 32) {
           // stop once a candidate is held and this chunk starts beyond its shell
