@@ -154,6 +154,25 @@ def whole_job_mlups(world, cells_per_rank, steps, ms_local, device=None):
     return world * cells_per_rank * steps / (ms_max * 1e-3) / 1e6, ms_max
 
 
+# The early horizon at which the store variants' phi is compared point by point: the droplets have
+# not met yet. After contact the flow is chaotic (a 2^-30 change of phi in one cell grows to
+# max|dphi| ~ 0.2 by step 2000 in FP32), so later comparisons use the droplet centroids.
+EARLY = 200
+
+
+def centroids(cfg, phi):
+    """phi-weighted mean x of the left and right halves of the box (one droplet each)."""
+    import numpy as np
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    p = np.asarray(phi).reshape(nz, ny, nx)
+    X = np.arange(nx, dtype=np.float64)
+    out = []
+    for sl in (slice(0, nx // 2), slice(nx // 2, nx)):
+        q = p[:, :, sl].sum(axis=(0, 1))
+        out.append(float((q * X[sl]).sum() / q.sum()))
+    return out
+
+
 def make_workload():
     from paper_2603_17481_gb300 import workloads as W
     cfg, phi, u = W.c3_head_on_3d()
@@ -262,6 +281,12 @@ def run_ours(args, world, rank, local):
 
     variants = {}
     if want_variants:
+        # FP32 reference at the early horizon (before the droplets meet)
+        ref = B.Lbm(cfg, store="f32", stream=stream.cuda_stream)
+        ref.init_fields(phi, u)
+        ref.step(EARLY)
+        ph32_early = ref.read_fields(want=("phi",))[0]
+        ref.close()
         for st in ("f16", "bf16"):
             s2 = B.Lbm(cfg, store=st, stream=stream.cuda_stream)
             s2.init_fields(phi, u)
@@ -281,13 +306,20 @@ def run_ours(args, world, rank, local):
             v_mlups = N * kv / (msv * 1e-3) / 1e6
             # phi after the same number of steps as the FP32 run, compared with it
             s2.init_fields(phi, u)
-            s2.step(n32)
+            s2.step(EARLY)
+            d_early = np.abs(s2.read_fields(want=("phi",))[0] - ph32_early)
+            s2.step(n32 - EARLY)
             ph2, _, _ = s2.read_fields(want=("phi",))
             variants[st] = {
                 "value": round(v_mlups, 1), "steps": kv,
                 "hydro_gbs": round(hydro_bytes_per_cell(Q, 2) * N / (hm / hn * 1e-3) / 1e9, 1),
                 "step_roofline_frac": round(v_mlups * 1e6 * step_bytes_per_cell(Q, 2) / (peak * 1e9), 4),
-                "max_abs_phi_diff_vs_f32_after_%d_steps" % n32: float(np.max(np.abs(ph2 - ph32))),
+                "phi_diff_vs_f32": {
+                    f"after_{EARLY}_steps": {"max": float(d_early.max()),
+                                             "q999": float(np.quantile(d_early, 0.999))},
+                    f"after_{n32}_steps": {"max": float(np.max(np.abs(ph2 - ph32))),
+                                           "centroid_max_cells": max(abs(a - b) for a, b in
+                                                                     zip(centroids(cfg, ph2), centroids(cfg, ph32)))}},
                 "phi_mass_drift": abs(s2.mass()[0] - m0) / abs(m0),
             }
             s2.close()
@@ -330,7 +362,8 @@ def run_ours(args, world, rank, local):
 
 
 SWEEP_WORKLOAD = ("batched sweep: {n} independent 3D D3Q19 collisions on grids drawn from {{48,64,80,96}}^3, "
-                  "R=L/6, W=4, density ratio 10, Weber log-uniform in [1,100] via speed, b ~ U[0,1]*2R")
+                  "R=L/6, W=4, density ratio 10, sigma=1e-3, Weber log-uniform in [1,100] via speed, "
+                  "b ~ U[0,1]*2R")
 
 
 def run_sweep(args, world, rank, local):

@@ -118,25 +118,23 @@ def c3_head_on_3d(nx=256, ny=128, nz=128, R=24.0, Q=19):
 SWEEP_GRIDS = (48, 64, 80, 96)
 
 
-def c4_sweep(n=512, seed=17481, u_max=0.1, we_min=1.0, we_max=100.0, grids=SWEEP_GRIDS):
+def c4_sweep(n=512, seed=17481, sigma=1e-3, we_min=1.0, we_max=100.0, grids=SWEEP_GRIDS):
     """Parameter sets of the batched sweep: ``n`` independent 3D D3Q19 collisions, density ratio 10.
 
-    Each case draws its cubic grid edge L from ``grids``, R = L / 6, a Weber number
-    We = rho_l U^2 (2R) / sigma log-uniform in [we_min, we_max] and an impact offset b ~ U(0, 1) 2R
-    along y. The Weber number is set through the speed: sigma = rho_l u_max^2 (2R) / we_max, so that
-    the relative speed U = u_max sqrt(We / we_max) stays within [u_max / 10, u_max] in lattice
-    units; A_rep = sigma. The droplets start 2R + 8 apart along x, moving at -+U/2.
-    Fields come from ``c4_fields``.
+    Case i draws from ``default_rng(seed + i)``: its cubic grid edge L from ``grids``, R = L / 6, a
+    Weber number We = rho_l U^2 (2R) / sigma log-uniform in [we_min, we_max], set through the
+    relative speed U = sqrt(We sigma / (rho_l 2R)) (U <= 0.08 for sigma = 1e-3), and an impact
+    offset b ~ U(0, 1) 2R along y. A_rep = sigma; viscosities as in the other collisions. The
+    droplets start 2R + 8 apart along x, moving at -+U/2. Fields come from ``c4_fields``.
     """
-    rng = np.random.default_rng(seed)
     out = []
     for i in range(n):
+        rng = np.random.default_rng(seed + i)
         L = int(grids[int(rng.integers(0, len(grids)))])
         R = L / 6.0
         we = float(math.exp(rng.uniform(math.log(we_min), math.log(we_max))))
         b = float(rng.uniform(0.0, 1.0)) * 2.0 * R
-        sigma = 1.0 * u_max * u_max * 2.0 * R / we_max
-        U = u_max * math.sqrt(we / we_max)
+        U = math.sqrt(we * sigma / (1.0 * 2.0 * R))
         cfg = base_config(3, L, L, L, 19, rho_g=0.1, sigma=sigma, A_rep=sigma, steps=1000)
         c = (L - 1) / 2.0
         sep = 2 * R + 8

@@ -22,7 +22,7 @@ def test_sweep_parameters():
         assert 1.0 <= c["weber"] <= 100.0 and 0.0 <= c["impact_offset"] <= 2 * R
         # We = rho_l U^2 (2R) / sigma is the drawn Weber number
         assert math.isclose(c["rho_l"] * c["speed"] ** 2 * 2 * R / c["sigma"], c["weber"], rel_tol=1e-12)
-        assert 0.01 <= c["speed"] <= 0.1
+        assert c["sigma"] == 1e-3 and c["speed"] <= 0.08
         (x0, y0, _), (x1, y1, _) = c["centers"]
         assert math.isclose(x1 - x0, 2 * R + 8) and math.isclose(y1 - y0, c["impact_offset"])
     # reproducible from the seed
@@ -62,3 +62,11 @@ def test_count_bubbles_of_generated_swarm():
     cfg, cs, rs = W.c5_swarm(L=96, nb=20, seed=9)
     phi, _ = W.c5_fields(cfg, cs, rs)
     assert bench.count_bubbles((phi < 0.5).reshape(96, 96, 96)) == len(cs)
+
+
+def test_centroids_of_two_droplets():
+    # lattice-symmetric centres, 24 cells from the halves' borders (profile tails below 1e-8)
+    cfg = W.base_config(3, 96, 16, 12, 19)
+    phi, _ = W.droplet_fields(cfg, [(24.0, 7.5, 5.5), (71.5, 7.5, 5.5)], [5.0, 5.0], [(0, 0, 0)] * 2)
+    c = bench.centroids(cfg, phi)
+    assert abs(c[0] - 24.0) < 1e-6 and abs(c[1] - 71.5) < 1e-6
