@@ -118,8 +118,9 @@ __device__ __forceinline__ int32_t face_transfer(const KParams &P, const int32_t
     const float ua = __ldg(u + AXIS * N + gx + (long long)n0x * (gy + (long long)n0y * gz));
     const float ub = __ldg(u + AXIS * N + qx + (long long)n0x * (qy + (long long)n0y * qz));
     const float uf = __fmul_rn(0.5f, __fadd_rn(ua, ub));
-    const long long up2 = uf >= 0.0f ? 2LL * v0 + s0 : 2LL * v1 - s1;
-    const float pup = __ll2float_rn(up2) * (0.5f * kInvQ30);
+    // upwind state; exact integer slopes, FP32 sum (no 64-bit conversion, which runs on the FP64 pipe)
+    const float pup = uf >= 0.0f ? (__int2float_rn(v0) + 0.5f * __int2float_rn(s0)) * kInvQ30
+                                 : (__int2float_rn(v1) - 0.5f * __int2float_rn(s1)) * kInvQ30;
     tau = __fadd_rn(tau, __fmul_rn(uf, pup));
   }
   return __float2int_rn(__fmul_rn(tau, kQ30));
@@ -227,15 +228,19 @@ k_phase(const KParams P, const int32_t *__restrict__ phi, const float *__restric
 // 3D: a block owns a 32 x 8 column of cells over zc planes (zc = 16, or 8 or 4 on grids too small
 // to fill the GPU with 16-plane columns) and marches along z, keeping ring
 // buffers of planes in shared memory. The D3Q27 weights factor as s(c_x) s(c_y) s(c_z) / 216, so
-//   RZ(k)   = phi(k-1) + 4 phi(k) + phi(k+1)         (exact, 64-bit)
-//   PSXY(k) = s_x s_y phi(k)                         (exact, 64-bit)
+//   RZ(k)   = phi(k-1) + 4 phi(k) + phi(k+1)
+//   PSXY(k) = s_x s_y phi(k)
 //   grad_x phi = (1/72) s_y [RZ(x+1) - RZ(x-1)],  grad_y phi = (1/72) s_x [RZ(y+1) - RZ(y-1)],
 //   grad_z phi = (1/72) [PSXY(k+1) - PSXY(k-1)],
 // and the face transfers of the header use the same planes: B_x (phi(p) - phi(p+e)) =
 // (1/36) s_y [RZ(p) - RZ(p+e)], B_y (...) = (1/6) [RZ(p) - RZ(p+e)], and the compressive sums
 // s_y s_z a_x, s_x s_z a_y, s_x s_y a_z from the z-smoothed planes AXZ, AYZ and the in-plane ASXY.
 // Every a value and every face transfer is computed once per block; the faces on block borders
-// are computed by both neighbours from identical inputs with the same rounded operations.
+// are computed by both neighbours from identical inputs with the same rounded operations. The plane
+// sums are FP32 over an FP32 copy of each phi plane (PF); the fixed-point planes (PH) give the exact
+// z-face differences and the update itself. Nothing here converts from 64-bit integers: those
+// conversions run on the FP64 pipe, which GB300 keeps narrow. Each face transfer is rounded once to
+// the 2^-30 grid, so the sum of phi is conserved exactly whatever the FP32 rounding inside.
 // ---------------------------------------------------------------------------------------------
 struct Phase3 {
   static constexpr int TX = 32, TY = 8, ZC = 16, NT = TX * TY;  // ZC: the largest z chunk
@@ -244,29 +249,37 @@ struct Phase3 {
   static constexpr int NC = TX * TY;
   static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
   static constexpr int NFLG = (ZC / 4) * (TY / 4);
-  static constexpr size_t smem = sizeof(long long) * (2 * NP + 4 * NQ) + sizeof(int32_t) * 4 * NP +
+  static constexpr size_t smem = sizeof(float) * (2 * NP + 4 * NQ) + sizeof(int32_t) * 4 * NP +
+                                 sizeof(float) * 4 * NP +
                                  sizeof(float) * (12 * NQ + 2 * NQ + 2 * NC + QX * TY + TX * QY + 2 * NC) +
                                  sizeof(int32_t) * (NFX + NFY + 2 * NC + NFLG);
   __device__ static __forceinline__ int pi(int lx, int ly) { return (ly + 2) * PX + lx + 2; }
   __device__ static __forceinline__ int qi(int lx, int ly) { return (ly + 1) * QX + lx + 1; }
 };
 
-__device__ __forceinline__ long long s141(long long a, long long b, long long c) { return a + 4 * b + c; }
+__device__ __forceinline__ float s141(float a, float b, float c) { return a + 4.0f * b + c; }
+
+__device__ __forceinline__ float minmod_f(float a, float b) {
+  if (a > 0.0f && b > 0.0f) return fminf(a, b);
+  if (a < 0.0f && b < 0.0f) return fmaxf(a, b);
+  return 0.0f;
+}
 
 __global__ void __launch_bounds__(Phase3::NT, 4)
 k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restrict__ u,
          int32_t *__restrict__ phi_out, int *__restrict__ tiles, int *__restrict__ ntiles, const int zc) {
   using G = Phase3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  long long *RZ = reinterpret_cast<long long *>(smem_raw);  // [2][NP]
-  long long *PS = RZ + 2 * G::NP;                            // [4][NQ]
-  int32_t *PH = reinterpret_cast<int32_t *>(PS + 4 * G::NQ);  // [4][NP]
-  float *A = reinterpret_cast<float *>(PH + 4 * G::NP);       // [4][3][NQ]
+  float *RZ = reinterpret_cast<float *>(smem_raw);           // [2][NP]
+  float *PS = RZ + 2 * G::NP;                                // [4][NQ]
+  int32_t *PH = reinterpret_cast<int32_t *>(PS + 4 * G::NQ);  // [4][NP] fixed point
+  float *PF = reinterpret_cast<float *>(PH + 4 * G::NP);      // [4][NP] FP32 copy
+  float *A = PF + 4 * G::NP;                                 // [4][3][NQ]
   float *AXZ = A + 12 * G::NQ;                               // [NQ]
   float *AYZ = AXZ + G::NQ;                                  // [NQ]
   float *ASXY = AYZ + G::NQ;                                 // [2][NC]
   float *UX = ASXY + 2 * G::NC;                              // [TY][QX]: lx -1..32
-  float *UY = UX + G::QX * G::TY;                            // [QY][TX]: ly -1..8
+  float *UY = UX + G::QX * G::TY;                            // [QY][TX]: ly -1..TY
   float *UZ = UY + G::TX * G::QY;                            // [2][NC]
   int32_t *TXF = reinterpret_cast<int32_t *>(UZ + 2 * G::NC);  // [TY][TX+1]
   int32_t *TYF = TXF + G::NFX;                                 // [TY+1][TX]
@@ -320,12 +333,17 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
     // S1: phi plane k+2; u_z plane k+1; u_x, u_y planes k (from registers), then prefetch k+1
     {
       int32_t *ph = PH + s4k2 * G::NP;
+      float *pf = PF + s4k2 * G::NP;
 #pragma unroll
       for (int h = 0; h < 2; h++) {
         const int r = wy + h * G::TY;
         if (r < G::PY) {
           ph[r * G::PX + lane] = rphi[2 * h];
-          if (lane < 4) ph[r * G::PX + 32 + lane] = rphi[2 * h + 1];
+          pf[r * G::PX + lane] = phi_of(rphi[2 * h]);
+          if (lane < 4) {
+            ph[r * G::PX + 32 + lane] = rphi[2 * h + 1];
+            pf[r * G::PX + 32 + lane] = phi_of(rphi[2 * h + 1]);
+          }
         }
       }
       UZ[((k + 1) & 1) * G::NC + tid] = ruz;
@@ -341,38 +359,39 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
     __syncthreads();
     // S2: RZ(k+1) and PSXY(k+2)
     {
-      const int32_t *p0 = PH + s4k * G::NP, *p1 = PH + s4k1 * G::NP, *p2 = PH + s4k2 * G::NP;
+      const float *p0 = PF + s4k * G::NP, *p1 = PF + s4k1 * G::NP, *p2 = PF + s4k2 * G::NP;
       if (k >= zb - 2) {
-        long long *rz = RZ + ((k + 1) & 1) * G::NP;
+        float *rz = RZ + ((k + 1) & 1) * G::NP;
         for (int t = tid; t < G::NP; t += G::NT) rz[t] = s141(p0[t], p1[t], p2[t]);
       }
-      long long *ps = PS + s4k2 * G::NQ;
+      float *ps = PS + s4k2 * G::NQ;
       for (int t = tid; t < G::NQ; t += G::NT) {
         const int c = G::pi(t % G::QX - 1, t / G::QX - 1);
-        const long long r0 = s141(p2[c - G::PX - 1], p2[c - G::PX], p2[c - G::PX + 1]);
-        const long long r1 = s141(p2[c - 1], p2[c], p2[c + 1]);
-        const long long r2 = s141(p2[c + G::PX - 1], p2[c + G::PX], p2[c + G::PX + 1]);
+        const float r0 = s141(p2[c - G::PX - 1], p2[c - G::PX], p2[c - G::PX + 1]);
+        const float r1 = s141(p2[c - 1], p2[c], p2[c + 1]);
+        const float r2 = s141(p2[c + G::PX - 1], p2[c + G::PX], p2[c + G::PX + 1]);
         ps[t] = s141(r0, r1, r2);
       }
     }
     __syncthreads();
     // S3: a(k+1) = phi (1 - phi) grad(phi) / (|grad(phi)| + eps_n)
     if (k >= zb - 2) {
-      const long long *rz = RZ + ((k + 1) & 1) * G::NP;
-      const long long *psp = PS + s4k2 * G::NQ, *psm = PS + s4k * G::NQ;
-      const int32_t *p1 = PH + s4k1 * G::NP;
+      const float *rz = RZ + ((k + 1) & 1) * G::NP;
+      const float *psp = PS + s4k2 * G::NQ, *psm = PS + s4k * G::NQ;
+      const float *p1 = PF + s4k1 * G::NP;
       float *a = A + s4k1 * 3 * G::NQ;
-      const float gs = kInvQ30 * (1.0f / 72.0f);
+      constexpr float gs = 1.0f / 72.0f;
       for (int t = tid; t < G::NQ; t += G::NT) {
         const int c = G::pi(t % G::QX - 1, t / G::QX - 1);
-        const long long gxi = s141(rz[c - G::PX + 1] - rz[c - G::PX - 1], rz[c + 1] - rz[c - 1],
+        const float g0 = gs * s141(rz[c - G::PX + 1] - rz[c - G::PX - 1], rz[c + 1] - rz[c - 1],
                                    rz[c + G::PX + 1] - rz[c + G::PX - 1]);
-        const long long gyi = s141(rz[c + G::PX - 1] - rz[c - G::PX - 1], rz[c + G::PX] - rz[c - G::PX],
+        const float g1 = gs * s141(rz[c + G::PX - 1] - rz[c - G::PX - 1], rz[c + G::PX] - rz[c - G::PX],
                                    rz[c + G::PX + 1] - rz[c - G::PX + 1]);
-        const long long gzi = psp[t] - psm[t];
-        const float g0 = __ll2float_rn(gxi) * gs, g1 = __ll2float_rn(gyi) * gs, g2 = __ll2float_rn(gzi) * gs;
-        const float ph = phi_of(p1[c]);
-        const float sc = ph * (1.0f - ph) / (sqrtf(g0 * g0 + g1 * g1 + g2 * g2) + P.eps_n);
+        const float g2 = gs * (psp[t] - psm[t]);
+        const float ph = p1[c];
+        const float gg = g0 * g0 + g1 * g1 + g2 * g2;
+        const float gn = gg > 0.0f ? gg * rsqrtf(gg) : 0.0f;
+        const float sc = __fdividef(ph * (1.0f - ph), gn + P.eps_n);
         a[t] = g0 * sc;
         a[G::NQ + t] = g1 * sc;
         a[2 * G::NQ + t] = g2 * sc;
@@ -402,56 +421,53 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
     __syncthreads();
     // S5: face transfers. x and y faces of plane k; z face between planes k and k+1
     {
-      const int32_t *p0 = PH + s4k * G::NP;
+      const float *p0 = PF + s4k * G::NP;
       if (k >= zb) {
-        const long long *rz = RZ + (k & 1) * G::NP;
-        const float dx_s = kInvQ30 * (1.0f / 36.0f), dy_s = kInvQ30 * (1.0f / 6.0f);
+        const float *rz = RZ + (k & 1) * G::NP;
+        constexpr float dx_s = 1.0f / 36.0f, dy_s = 1.0f / 6.0f;
         for (int t = tid; t < G::NFX; t += G::NT) {
           const int lx = t % (G::TX + 1) - 1, ly = t / (G::TX + 1);
           const int c = G::pi(lx, ly);
-          const long long di = s141(rz[c - G::PX] - rz[c - G::PX + 1], rz[c] - rz[c + 1],
-                                    rz[c + G::PX] - rz[c + G::PX + 1]);
-          float tau = __fmul_rn(D, __fmul_rn(__ll2float_rn(di), dx_s));
+          const float di = s141(rz[c - G::PX] - rz[c - G::PX + 1], rz[c] - rz[c + 1],
+                                rz[c + G::PX] - rz[c + G::PX + 1]);
+          float tau = __fmul_rn(D, __fmul_rn(di, dx_s));
           const int q = G::qi(lx, ly);
           const float cs = __fadd_rn(__fadd_rn(__fadd_rn(AXZ[q - G::QX], AXZ[q - G::QX + 1]),
                                                __fmul_rn(4.f, __fadd_rn(AXZ[q], AXZ[q + 1]))),
                                      __fadd_rn(AXZ[q + G::QX], AXZ[q + G::QX + 1]));
           tau = __fadd_rn(tau, __fmul_rn(k3, __fmul_rn(cs, 1.0f / 216.0f)));
-          const int32_t vm = p0[c - 1], v0 = p0[c], v1 = p0[c + 1], vp = p0[c + 2];
-          const int32_t sl = minmod_i(v0 - vm, v1 - v0), sr = minmod_i(v1 - v0, vp - v1);
+          const float vm = p0[c - 1], v0 = p0[c], v1 = p0[c + 1], vp = p0[c + 2];
           const float uf = __fmul_rn(0.5f, __fadd_rn(UX[ly * G::QX + lx + 1], UX[ly * G::QX + lx + 2]));
-          const long long up2 = uf >= 0.0f ? 2LL * v0 + sl : 2LL * v1 - sr;
-          tau = __fadd_rn(tau, __fmul_rn(uf, __ll2float_rn(up2) * (0.5f * kInvQ30)));
+          const float up = uf >= 0.0f ? v0 + 0.5f * minmod_f(v0 - vm, v1 - v0) : v1 - 0.5f * minmod_f(v1 - v0, vp - v1);
+          tau = __fadd_rn(tau, __fmul_rn(uf, up));
           TXF[t] = __float2int_rn(__fmul_rn(tau, kQ30));
         }
         for (int t = tid; t < G::NFY; t += G::NT) {
           const int lx = t % G::TX, ly = t / G::TX - 1;
           const int c = G::pi(lx, ly);
-          float tau = __fmul_rn(D, __fmul_rn(__ll2float_rn(rz[c] - rz[c + G::PX]), dy_s));
+          float tau = __fmul_rn(D, __fmul_rn(rz[c] - rz[c + G::PX], dy_s));
           const int q = G::qi(lx, ly);
           const float cs = __fadd_rn(__fadd_rn(__fadd_rn(AYZ[q - 1], AYZ[q - 1 + G::QX]),
                                                __fmul_rn(4.f, __fadd_rn(AYZ[q], AYZ[q + G::QX]))),
                                      __fadd_rn(AYZ[q + 1], AYZ[q + 1 + G::QX]));
           tau = __fadd_rn(tau, __fmul_rn(k3, __fmul_rn(cs, 1.0f / 216.0f)));
-          const int32_t vm = p0[c - G::PX], v0 = p0[c], v1 = p0[c + G::PX], vp = p0[c + 2 * G::PX];
-          const int32_t sl = minmod_i(v0 - vm, v1 - v0), sr = minmod_i(v1 - v0, vp - v1);
+          const float vm = p0[c - G::PX], v0 = p0[c], v1 = p0[c + G::PX], vp = p0[c + 2 * G::PX];
           const float uf = __fmul_rn(0.5f, __fadd_rn(UY[(ly + 1) * G::TX + lx], UY[(ly + 2) * G::TX + lx]));
-          const long long up2 = uf >= 0.0f ? 2LL * v0 + sl : 2LL * v1 - sr;
-          tau = __fadd_rn(tau, __fmul_rn(uf, __ll2float_rn(up2) * (0.5f * kInvQ30)));
+          const float up = uf >= 0.0f ? v0 + 0.5f * minmod_f(v0 - vm, v1 - v0) : v1 - 0.5f * minmod_f(v1 - v0, vp - v1);
+          tau = __fadd_rn(tau, __fmul_rn(uf, up));
           TYF[t] = __float2int_rn(__fmul_rn(tau, kQ30));
         }
       }
       if (k >= zb - 1) {
         const int lx = tid & 31, ly = tid >> 5;
         const int c = G::pi(lx, ly);
-        const int32_t vm = PH[s4km * G::NP + c], v0 = p0[c], v1 = PH[s4k1 * G::NP + c], vp = PH[s4k2 * G::NP + c];
-        float tau = __fmul_rn(D, dphi_of(v0, v1));
+        float tau = __fmul_rn(D, dphi_of(PH[s4k * G::NP + c], PH[s4k1 * G::NP + c]));
+        const float vm = PF[s4km * G::NP + c], v0 = p0[c], v1 = PF[s4k1 * G::NP + c], vp = PF[s4k2 * G::NP + c];
         const float cs = __fadd_rn(ASXY[(k & 1) * G::NC + tid], ASXY[((k + 1) & 1) * G::NC + tid]);
         tau = __fadd_rn(tau, __fmul_rn(k3, __fmul_rn(cs, 1.0f / 216.0f)));
-        const int32_t sl = minmod_i(v0 - vm, v1 - v0), sr = minmod_i(v1 - v0, vp - v1);
         const float uf = __fmul_rn(0.5f, __fadd_rn(UZ[(k & 1) * G::NC + tid], UZ[((k + 1) & 1) * G::NC + tid]));
-        const long long up2 = uf >= 0.0f ? 2LL * v0 + sl : 2LL * v1 - sr;
-        tau = __fadd_rn(tau, __fmul_rn(uf, __ll2float_rn(up2) * (0.5f * kInvQ30)));
+        const float up = uf >= 0.0f ? v0 + 0.5f * minmod_f(v0 - vm, v1 - v0) : v1 - 0.5f * minmod_f(v1 - v0, vp - v1);
+        tau = __fadd_rn(tau, __fmul_rn(uf, up));
         TZF[((k + 1) & 1) * G::NC + tid] = __float2int_rn(__fmul_rn(tau, kQ30));
       }
     }
