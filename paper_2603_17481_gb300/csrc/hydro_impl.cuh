@@ -28,10 +28,16 @@
 
 #include "launch.h"
 
+// Resident blocks per SM (256 threads each) that the register allocation is sized for: 5 (48
+// registers, no spills, 1.05x faster than 4 on D3Q19) except D3Q27, which spills below 56.
+#ifndef LBM_HYDRO_MINB
+#define LBM_HYDRO_MINB 5
+#endif
+
 namespace lbm {
 
 template <class L, int S, int MODE>
-__global__ void __launch_bounds__(Tile<L::D>::X * Tile<L::D>::Y * Tile<L::D>::Z, 4)
+__global__ void __launch_bounds__(Tile<L::D>::X * Tile<L::D>::Y * Tile<L::D>::Z, L::Q >= 27 ? 4 : LBM_HYDRO_MINB)
 k_hydro(const KParams P, const typename Store<S>::T *__restrict__ src, typename Store<S>::T *__restrict__ dst,
         const int32_t *__restrict__ phi, const float4 *__restrict__ frep, float *__restrict__ u_out,
         float *__restrict__ ps_out, int *__restrict__ reset) {

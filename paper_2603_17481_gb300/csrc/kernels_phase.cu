@@ -291,12 +291,35 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
   const long long N = P.N;
   const int x0 = blockIdx.x * G::TX, y0 = blockIdx.y * G::TY;
   const int zb = blockIdx.z * zc, ze = min(zb + zc, nz);
-  const float D = P.Dlap * (1.0f / 6.0f);
-  const float k3 = P.kc * kCs2 * 3.0f;  // 3 kappa
+  // face coefficients: D of the z link, with the 1/36 (x) and 1/6 (y) of the smoothed differences;
+  // 3 kappa / 216 on the smoothed compressive sums
+  const float D = P.Dlap * (1.0f / 6.0f), Dx = D * (1.0f / 36.0f), Dy = D * (1.0f / 6.0f);
+  const float k3s = P.kc * kCs2 * 3.0f * (1.0f / 216.0f);
   // this thread's x columns for plane loads: phi planes (lx = lane - 2, and 30..33 for lanes 0..3),
   // u_x planes (lx = lane - 1, and 31..32 for lanes 0..1)
   const int xa = wrapn(x0 + lane - 2, nx), xb = wrapn(x0 + 30 + (lane & 3), nx);
   const int ua = wrapn(x0 + lane - 1, nx), ub = wrapn(x0 + 31 + (lane & 1), nx);
+  const int xc = wrapn(x0 + lane, nx);
+  // row offsets within a plane (constant over the march): phi rows y0 + r - 2, u_y rows y0 + r - 1
+  int yph[2], yuy[2];
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    yph[h] = nx * wrapn(y0 + wy + h * G::TY - 2, ny);
+    yuy[h] = nx * wrapn(y0 + wy + h * G::TY - 1, ny);
+  }
+  const int yown = nx * wrapn(y0 + wy, ny);
+  const long long plane = (long long)nx * ny;
+  // shared-memory index of the halo-1 entries t = tid and tid + NT, and of the x faces t = tid and
+  // tid + NT as (plane index, row): also constant over the march
+  static_assert(G::NQ <= 2 * G::NT && G::NFX <= 2 * G::NT && G::NFY <= 2 * G::NT, "two entries per thread");
+  int cq[2], cfx[2], lfx[2];
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const int t = tid + h * G::NT;
+    cq[h] = G::pi(t % G::QX - 1, t / G::QX - 1);
+    lfx[h] = t / (G::TX + 1);
+    cfx[h] = G::pi(t % (G::TX + 1) - 1, lfx[h]);
+  }
   if (tid < G::NFLG) FLG[tid] = 0;
 
   // Plane loads are software-pipelined: the values for iteration k + 1 (phi plane k + 3, u_z plane
@@ -304,26 +327,21 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
   int32_t rphi[4];
   float ruz, rux[2], ruy[2];
   auto prefetch = [&](int kk) {
-    const int Z = wrapn(kk + 2, nz);
+    const int32_t *pp = phi + plane * wrapn(kk + 2, nz);
 #pragma unroll
     for (int h = 0; h < 2; h++) {
-      const int r = wy + h * G::TY;
-      if (r < G::PY) {
-        const long long row = (long long)nx * (wrapn(y0 + r - 2, ny) + (long long)ny * Z);
-        rphi[2 * h] = phi[row + xa];
-        if (lane < 4) rphi[2 * h + 1] = phi[row + xb];
+      if (wy + h * G::TY < G::PY) {
+        rphi[2 * h] = pp[yph[h] + xa];
+        if (lane < 4) rphi[2 * h + 1] = pp[yph[h] + xb];
       }
     }
-    const int Zu = wrapn(kk + 1, nz), Zk = wrapn(kk, nz);
-    const int xc = wrapn(x0 + lane, nx);
-    ruz = __ldg(u + 2 * N + (long long)nx * (wrapn(y0 + wy, ny) + (long long)ny * Zu) + xc);
-    const long long rowk = (long long)nx * (wrapn(y0 + wy, ny) + (long long)ny * Zk);
-    rux[0] = __ldg(u + rowk + ua);
-    if (lane < 2) rux[1] = __ldg(u + rowk + ub);
+    const float *uk = u + plane * wrapn(kk, nz);
+    ruz = __ldg(u + 2 * N + plane * wrapn(kk + 1, nz) + yown + xc);
+    rux[0] = __ldg(uk + yown + ua);
+    if (lane < 2) rux[1] = __ldg(uk + yown + ub);
 #pragma unroll
     for (int h = 0; h < 2; h++) {
-      const int r = wy + h * G::TY;
-      if (r < G::QY) ruy[h] = __ldg(u + N + (long long)nx * (wrapn(y0 + r - 1, ny) + (long long)ny * Zk) + xc);
+      if (wy + h * G::TY < G::QY) ruy[h] = __ldg(uk + N + yuy[h] + xc);
     }
   };
   prefetch(zb - 4);
@@ -365,8 +383,11 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
         for (int t = tid; t < G::NP; t += G::NT) rz[t] = s141(p0[t], p1[t], p2[t]);
       }
       float *ps = PS + s4k2 * G::NQ;
-      for (int t = tid; t < G::NQ; t += G::NT) {
-        const int c = G::pi(t % G::QX - 1, t / G::QX - 1);
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int t = tid + h * G::NT;
+        if (t >= G::NQ) break;
+        const int c = cq[h];
         const float r0 = s141(p2[c - G::PX - 1], p2[c - G::PX], p2[c - G::PX + 1]);
         const float r1 = s141(p2[c - 1], p2[c], p2[c + 1]);
         const float r2 = s141(p2[c + G::PX - 1], p2[c + G::PX], p2[c + G::PX + 1]);
@@ -381,8 +402,11 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
       const float *p1 = PF + s4k1 * G::NP;
       float *a = A + s4k1 * 3 * G::NQ;
       constexpr float gs = 1.0f / 72.0f;
-      for (int t = tid; t < G::NQ; t += G::NT) {
-        const int c = G::pi(t % G::QX - 1, t / G::QX - 1);
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int t = tid + h * G::NT;
+        if (t >= G::NQ) break;
+        const int c = cq[h];
         const float g0 = gs * s141(rz[c - G::PX + 1] - rz[c - G::PX - 1], rz[c + 1] - rz[c - 1],
                                    rz[c + G::PX + 1] - rz[c + G::PX - 1]);
         const float g1 = gs * s141(rz[c + G::PX - 1] - rz[c - G::PX - 1], rz[c + G::PX] - rz[c - G::PX],
@@ -405,16 +429,16 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
       {
         const int lx = tid & 31, ly = tid >> 5;
         const int c = G::qi(lx, ly);
-        const float r0 = __fadd_rn(__fadd_rn(az[c - G::QX - 1], __fmul_rn(4.f, az[c - G::QX])), az[c - G::QX + 1]);
-        const float r1 = __fadd_rn(__fadd_rn(az[c - 1], __fmul_rn(4.f, az[c])), az[c + 1]);
-        const float r2 = __fadd_rn(__fadd_rn(az[c + G::QX - 1], __fmul_rn(4.f, az[c + G::QX])), az[c + G::QX + 1]);
-        asxy[tid] = __fadd_rn(__fadd_rn(r0, __fmul_rn(4.f, r1)), r2);
+        const float r0 = s141(az[c - G::QX - 1], az[c - G::QX], az[c - G::QX + 1]);
+        const float r1 = s141(az[c - 1], az[c], az[c + 1]);
+        const float r2 = s141(az[c + G::QX - 1], az[c + G::QX], az[c + G::QX + 1]);
+        asxy[tid] = s141(r0, r1, r2);
       }
       if (k >= zb) {
         const float *am = A + s4km * 3 * G::NQ, *a0 = A + s4k * 3 * G::NQ, *ap = A + s4k1 * 3 * G::NQ;
         for (int t = tid; t < G::NQ; t += G::NT) {
-          AXZ[t] = __fadd_rn(__fadd_rn(am[t], __fmul_rn(4.f, a0[t])), ap[t]);
-          AYZ[t] = __fadd_rn(__fadd_rn(am[G::NQ + t], __fmul_rn(4.f, a0[G::NQ + t])), ap[G::NQ + t]);
+          AXZ[t] = s141(am[t], a0[t], ap[t]);
+          AYZ[t] = s141(am[G::NQ + t], a0[G::NQ + t], ap[G::NQ + t]);
         }
       }
     }
@@ -424,51 +448,44 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
       const float *p0 = PF + s4k * G::NP;
       if (k >= zb) {
         const float *rz = RZ + (k & 1) * G::NP;
-        constexpr float dx_s = 1.0f / 36.0f, dy_s = 1.0f / 6.0f;
-        for (int t = tid; t < G::NFX; t += G::NT) {
-          const int lx = t % (G::TX + 1) - 1, ly = t / (G::TX + 1);
-          const int c = G::pi(lx, ly);
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          const int t = tid + h * G::NT;
+          if (t >= G::NFX) break;
+          const int c = cfx[h], ly = lfx[h];
+          const int lx = c - G::pi(0, ly);
           const float di = s141(rz[c - G::PX] - rz[c - G::PX + 1], rz[c] - rz[c + 1],
                                 rz[c + G::PX] - rz[c + G::PX + 1]);
-          float tau = __fmul_rn(D, __fmul_rn(di, dx_s));
           const int q = G::qi(lx, ly);
-          const float cs = __fadd_rn(__fadd_rn(__fadd_rn(AXZ[q - G::QX], AXZ[q - G::QX + 1]),
-                                               __fmul_rn(4.f, __fadd_rn(AXZ[q], AXZ[q + 1]))),
-                                     __fadd_rn(AXZ[q + G::QX], AXZ[q + G::QX + 1]));
-          tau = __fadd_rn(tau, __fmul_rn(k3, __fmul_rn(cs, 1.0f / 216.0f)));
+          const float cs = s141(AXZ[q - G::QX] + AXZ[q - G::QX + 1], AXZ[q] + AXZ[q + 1],
+                                AXZ[q + G::QX] + AXZ[q + G::QX + 1]);
           const float vm = p0[c - 1], v0 = p0[c], v1 = p0[c + 1], vp = p0[c + 2];
-          const float uf = __fmul_rn(0.5f, __fadd_rn(UX[ly * G::QX + lx + 1], UX[ly * G::QX + lx + 2]));
+          const float uf = 0.5f * (UX[ly * G::QX + lx + 1] + UX[ly * G::QX + lx + 2]);
           const float up = uf >= 0.0f ? v0 + 0.5f * minmod_f(v0 - vm, v1 - v0) : v1 - 0.5f * minmod_f(v1 - v0, vp - v1);
-          tau = __fadd_rn(tau, __fmul_rn(uf, up));
-          TXF[t] = __float2int_rn(__fmul_rn(tau, kQ30));
+          TXF[t] = __float2int_rn(kQ30 * fmaf(Dx, di, fmaf(k3s, cs, uf * up)));
         }
         for (int t = tid; t < G::NFY; t += G::NT) {
           const int lx = t % G::TX, ly = t / G::TX - 1;
           const int c = G::pi(lx, ly);
-          float tau = __fmul_rn(D, __fmul_rn(rz[c] - rz[c + G::PX], dy_s));
+          const float di = rz[c] - rz[c + G::PX];
           const int q = G::qi(lx, ly);
-          const float cs = __fadd_rn(__fadd_rn(__fadd_rn(AYZ[q - 1], AYZ[q - 1 + G::QX]),
-                                               __fmul_rn(4.f, __fadd_rn(AYZ[q], AYZ[q + G::QX]))),
-                                     __fadd_rn(AYZ[q + 1], AYZ[q + 1 + G::QX]));
-          tau = __fadd_rn(tau, __fmul_rn(k3, __fmul_rn(cs, 1.0f / 216.0f)));
+          const float cs = s141(AYZ[q - 1] + AYZ[q - 1 + G::QX], AYZ[q] + AYZ[q + G::QX],
+                                AYZ[q + 1] + AYZ[q + 1 + G::QX]);
           const float vm = p0[c - G::PX], v0 = p0[c], v1 = p0[c + G::PX], vp = p0[c + 2 * G::PX];
-          const float uf = __fmul_rn(0.5f, __fadd_rn(UY[(ly + 1) * G::TX + lx], UY[(ly + 2) * G::TX + lx]));
+          const float uf = 0.5f * (UY[(ly + 1) * G::TX + lx] + UY[(ly + 2) * G::TX + lx]);
           const float up = uf >= 0.0f ? v0 + 0.5f * minmod_f(v0 - vm, v1 - v0) : v1 - 0.5f * minmod_f(v1 - v0, vp - v1);
-          tau = __fadd_rn(tau, __fmul_rn(uf, up));
-          TYF[t] = __float2int_rn(__fmul_rn(tau, kQ30));
+          TYF[t] = __float2int_rn(kQ30 * fmaf(Dy, di, fmaf(k3s, cs, uf * up)));
         }
       }
       if (k >= zb - 1) {
         const int lx = tid & 31, ly = tid >> 5;
         const int c = G::pi(lx, ly);
-        float tau = __fmul_rn(D, dphi_of(PH[s4k * G::NP + c], PH[s4k1 * G::NP + c]));
+        const float di = dphi_of(PH[s4k * G::NP + c], PH[s4k1 * G::NP + c]);
         const float vm = PF[s4km * G::NP + c], v0 = p0[c], v1 = PF[s4k1 * G::NP + c], vp = PF[s4k2 * G::NP + c];
-        const float cs = __fadd_rn(ASXY[(k & 1) * G::NC + tid], ASXY[((k + 1) & 1) * G::NC + tid]);
-        tau = __fadd_rn(tau, __fmul_rn(k3, __fmul_rn(cs, 1.0f / 216.0f)));
-        const float uf = __fmul_rn(0.5f, __fadd_rn(UZ[(k & 1) * G::NC + tid], UZ[((k + 1) & 1) * G::NC + tid]));
+        const float cs = ASXY[(k & 1) * G::NC + tid] + ASXY[((k + 1) & 1) * G::NC + tid];
+        const float uf = 0.5f * (UZ[(k & 1) * G::NC + tid] + UZ[((k + 1) & 1) * G::NC + tid]);
         const float up = uf >= 0.0f ? v0 + 0.5f * minmod_f(v0 - vm, v1 - v0) : v1 - 0.5f * minmod_f(v1 - v0, vp - v1);
-        tau = __fadd_rn(tau, __fmul_rn(uf, up));
-        TZF[((k + 1) & 1) * G::NC + tid] = __float2int_rn(__fmul_rn(tau, kQ30));
+        TZF[((k + 1) & 1) * G::NC + tid] = __float2int_rn(kQ30 * fmaf(D, di, fmaf(k3s, cs, uf * up)));
       }
     }
     __syncthreads();
