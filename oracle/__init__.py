@@ -90,6 +90,8 @@ def lib():
             L.orc_moments.argtypes = [_P, _D, _D, _D, _D]
             L.orc_step.argtypes = [_P, _D, _D, ctypes.c_int, _D]
             L.orc_step.restype = ctypes.c_int
+            L.orc_nci_diagnostics.argtypes = [_P, _D, _D]
+            L.orc_nci_diagnostics.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -207,6 +209,19 @@ def nci(P: OrcParams, phi):
     marg = np.zeros(N)
     lib().orc_nci(ctypes.byref(P), _d(phi), part.ctypes.data_as(_I), _d(frep), _d(marg))
     return part, frep, marg
+
+
+def nci_diagnostics(P: OrcParams, phi) -> dict:
+    """Film statistics of Sec. 3.3 on phi: V_film, sum |F_rep.n|, sum |F_cap.n|, max |F_rep|,
+    sum |F_rep|, and from them R_n (Eq. 74; 0 when there is no film) and the film mean of |F_rep|."""
+    N = ncells(P)
+    phi = _f64(phi, (N,))
+    out = np.zeros(5)
+    if lib().orc_nci_diagnostics(ctypes.byref(P), _d(phi), _d(out)):
+        raise MemoryError("oracle diagnostics failed to allocate")
+    v, srn, scn, fmax, sabs = (float(x) for x in out)
+    return {"V_film": v, "sum_rep_n": srn, "sum_cap_n": scn, "max_rep": fmax, "sum_rep": sabs,
+            "R_n": srn / scn if scn > 0 else 0.0, "mean_rep": sabs / v if v > 0 else 0.0}
 
 
 def phi_update(P: OrcParams, phi, u) -> np.ndarray:

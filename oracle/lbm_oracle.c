@@ -628,3 +628,43 @@ int orc_step(const orc_params *P, double *f, double *phi, int nsteps, double *u_
   free(fpost); free(u); free(phin);
   return 0;
 }
+
+/* Eq. 74 and the film statistics of Sec. 3.3: one pass over the cells that have a partner. */
+int orc_nci_diagnostics(const orc_params *P, const double *phi, double *out) {
+  const long N = ncells(P);
+  int *partner = (int *)malloc(sizeof(int) * 3 * N);
+  double *frep = (double *)malloc(sizeof(double) * 3 * N);
+  double *grad = (double *)malloc(sizeof(double) * 3 * N);
+  double *lap = (double *)malloc(sizeof(double) * N);
+  if (!partner || !frep || !grad || !lap) {
+    free(partner); free(frep); free(grad); free(lap);
+    return -1;
+  }
+  orc_nci(P, phi, partner, frep, NULL);
+  orc_grad_iso(P, phi, grad);
+  orc_lap_iso(P, phi, lap);
+  const double beta = 12.0 * P->sigma / P->eps, kap = 1.5 * P->sigma * P->eps;
+  double vfilm = 0, srn = 0, scn = 0, fmax = 0, sabs = 0;
+  for (long n = 0; n < N; n++) {
+    if (partner[3 * n] == INT_MIN) continue;
+    double g2 = 0;
+    for (int a = 0; a < 3; a++) g2 += grad[a * N + n] * grad[a * N + n];
+    const double gn = sqrt(g2);
+    const double muphi = 4.0 * beta * phi[n] * (phi[n] - 1.0) * (phi[n] - 0.5) - kap * lap[n];
+    double rn = 0, cn = 0, fr2 = 0;
+    for (int a = 0; a < 3; a++) {
+      const double na = grad[a * N + n] / (gn + P->eps_n);
+      rn += frep[a * N + n] * na;
+      cn += muphi * grad[a * N + n] * na;
+      fr2 += frep[a * N + n] * frep[a * N + n];
+    }
+    vfilm += 1.0;
+    srn += fabs(rn);
+    scn += fabs(cn);
+    sabs += sqrt(fr2);
+    if (sqrt(fr2) > fmax) fmax = sqrt(fr2);
+  }
+  out[0] = vfilm; out[1] = srn; out[2] = scn; out[3] = fmax; out[4] = sabs;
+  free(partner); free(frep); free(grad); free(lap);
+  return 0;
+}

@@ -80,6 +80,14 @@ void orc_moments(const orc_params *P, const double *f, const double *phi, double
  * last step (the one that advected phi). Returns 0, or -1 on allocation failure. */
 int orc_step(const orc_params *P, double *f, double *phi, int nsteps, double *u_last);
 
+/* Self-tuning diagnostics of the near-contact interaction (Sec. 3.3, Eq. 74) on phi, over the film
+ * region Omega_film = {chi = 1} (cells with a partner, Sec. 2.3.2), with n the normal of Eq. 57,
+ * F_rep of Eq. 73 and the capillary force F_cap = mu_phi grad(phi) of Eq. 19 (mu_phi of reading R3):
+ *   out[0] = V_film (number of film cells; dV = 1),  out[1] = sum |F_rep . n|,
+ *   out[2] = sum |F_cap . n|,  out[3] = max |F_rep|,  out[4] = sum |F_rep|.
+ * R_n = out[1] / out[2] and <|F_rep|>_film = out[4] / out[0]. Returns 0, or -1 on allocation failure. */
+int orc_nci_diagnostics(const orc_params *P, const double *phi, double *out);
+
 #ifdef __cplusplus
 }
 #endif
