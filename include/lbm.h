@@ -141,6 +141,15 @@ int lbm_mass_noalloc(lbm_ctx *ctx, double *phi_mass, double *mom);
  * chi = 0) and the repulsive force density F_rep (3N). Either pointer may be NULL. */
 int lbm_read_nci(lbm_ctx *ctx, int32_t *partner, double *frep);
 
+/* Near-contact film statistics of the current phi (Sec. 3.3, Eq. 74): the near-contact pass is run
+ * on the current phi, then, over the film Omega_film = {chi = 1} with n the normal of Eq. 57 and
+ * F_cap = mu_phi grad(phi) (Eq. 19), FP64 sums in a fixed order give
+ *   out[0] V_film (cells), out[1] sum |F_rep . n|, out[2] sum |F_cap . n|, out[3] max |F_rep|,
+ *   out[4] sum |F_rep|, out[5] R_n = out[1] / out[2] (0 without film), out[6] out[4] / out[0].
+ * out: 7 doubles (host), written on success; all zero when the near-contact model is off.
+ * Allocates 24 KB of device scratch on the first call. Synchronises the context's stream. */
+int lbm_nci_diagnostics(lbm_ctx *ctx, double *out);
+
 /* Batches: independent contexts advanced together (a parameter sweep of uneven cases; no
  * counterpart in the paper, which runs one case at a time). One CUDA graph holds two steps of
  * every context, the contexts spread over nstreams concurrent branches, so that small cases fill

@@ -72,6 +72,7 @@ def load():
     L.lbm_mass.argtypes = [_VP, _VP, _VP]
     L.lbm_read_nci.argtypes = [_VP, _VP, _VP]
     L.lbm_mass_noalloc.argtypes = [_VP, _VP, _VP]
+    L.lbm_nci_diagnostics.argtypes = [_VP, _VP]
     L.lbm_batch_create.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.POINTER(_VP)]
     L.lbm_batch_step.argtypes = [_VP, ctypes.c_int]
     L.lbm_batch_synchronize.argtypes = [_VP]
@@ -88,6 +89,7 @@ def load():
     for name in ("lbm_create", "lbm_set_stream", "lbm_init_fields", "lbm_set_state", "lbm_get_state",
                  "lbm_step", "lbm_read_fields", "lbm_mass", "lbm_mass_noalloc", "lbm_read_nci", "lbm_synchronize",
                  "lbm_profile", "lbm_profile_read", "lbm_lattice", "lbm_batch_create", "lbm_batch_step",
+                 "lbm_nci_diagnostics",
                  "lbm_batch_synchronize"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -222,6 +224,15 @@ def lbm_read_nci(ctx: int, N: int):
     return part, frep
 
 
+DIAG_KEYS = ("V_film", "sum_rep_n", "sum_cap_n", "max_rep", "sum_rep", "R_n", "mean_rep")
+
+
+def lbm_nci_diagnostics(ctx: int) -> dict:
+    out = np.zeros(7)
+    _check(load().lbm_nci_diagnostics(_VP(ctx), out.ctypes.data_as(_VP)), "lbm_nci_diagnostics")
+    return dict(zip(DIAG_KEYS, (float(v) for v in out)))
+
+
 def lbm_synchronize(ctx: int) -> None:
     _check(load().lbm_synchronize(_VP(ctx)), "lbm_synchronize")
 
@@ -346,6 +357,9 @@ class Lbm:
 
     def synchronize(self):
         lbm_synchronize(self.ctx)
+
+    def nci_diagnostics(self):
+        return lbm_nci_diagnostics(self.ctx)
 
     def profile(self, enable=True):
         lbm_profile(self.ctx, enable)

@@ -32,6 +32,7 @@ struct lbm_ctx {
   int *ntiles = nullptr;  // 2 counters, one per phi buffer
   int nci_blocks = 0;
   lbm::ReduceOut *red_part = nullptr, *red_out = nullptr;
+  lbm::DiagOut *diag_part = nullptr, *diag_out = nullptr;  // film statistics, on first use
   int cur = 0;        // population buffer holding the current state
   int pcur = 0;       // phi buffer holding phi^n
   bool initialised = false;

@@ -266,4 +266,101 @@ cudaError_t launch_reduce(const KParams &P, const int32_t *phi, const float *u, 
   return cudaGetLastError();
 }
 
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Film statistics of Sec. 3.3 (Eq. 74): per film cell, n = grad(phi) / (|grad(phi)| + eps_n) and
+// F_cap = mu_phi grad(phi) from the isotropic stencils (Eqs. 19, 22, 23), in FP32 as in the hydro
+// kernel; sums in FP64 over a fixed grid, then a fixed tree.
+template <int DIM>
+__global__ void __launch_bounds__(kReduceThreads)
+k_nci_diag_partial(const KParams P, const int32_t *__restrict__ phi, const float4 *__restrict__ frep,
+                   DiagOut *__restrict__ partials) {
+  using SL = typename StencilOf<DIM>::type;
+  double vf = 0.0, srn = 0.0, scn = 0.0, fmx = 0.0, sab = 0.0;
+  const int nx = P.nx, ny = P.ny, nz = P.nz;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < P.N; n += stride) {
+    const int32_t v = phi[n];
+    if (!(q_gate_value(v) >= P.q_th)) continue;
+    const float4 fr = frep[n];
+    if (!(fr.w > 0.5f)) continue;
+    const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long long)nx * ny));
+    const float ph = phi_of(v);
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f, lap = 0.f;
+#pragma unroll
+    for (int i = 1; i < SL::Q; i++) {
+      if (!positive<SL>(i)) continue;
+      const int c0 = SL::c(i, 0), c1 = SL::c(i, 1), c2 = SL::c(i, 2);
+      const long long ip = wrapn(x + c0, nx) + (long long)nx * (wrapn(y + c1, ny) + (long long)ny * wrapn(z + c2, nz));
+      const long long im = wrapn(x - c0, nx) + (long long)nx * (wrapn(y - c1, ny) + (long long)ny * wrapn(z - c2, nz));
+      const float vp = phi_of(phi[ip]), vm = phi_of(phi[im]);
+      const float d = SL::w(i) * (vp - vm);
+      g0 += c0 * d;
+      g1 += c1 * d;
+      g2 += c2 * d;
+      lap += SL::w(i) * ((vp - ph) + (vm - ph));
+    }
+    g0 *= 3.0f; g1 *= 3.0f; g2 *= 3.0f;
+    lap *= 6.0f;
+    const float muphi = P.beta4 * ph * (ph - 1.0f) * (ph - 0.5f) - P.kap * lap;
+    const float gg = g0 * g0 + g1 * g1 + g2 * g2;
+    const float inv = 1.0f / (sqrtf(gg) + P.eps_n);
+    const double rn = (double)((fr.x * g0 + fr.y * g1 + fr.z * g2) * inv);
+    const double cn = (double)(muphi * gg * inv);
+    const double fa = sqrt((double)fr.x * fr.x + (double)fr.y * fr.y + (double)fr.z * fr.z);
+    vf += 1.0;
+    srn += fabs(rn);
+    scn += fabs(cn);
+    sab += fa;
+    fmx = fmax(fmx, fa);
+  }
+  __shared__ double sm[5][kReduceThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  vf = warp_sum(vf); srn = warp_sum(srn); scn = warp_sum(scn); sab = warp_sum(sab); fmx = warp_max(fmx);
+  if (lane == 0) {
+    sm[0][wid] = vf; sm[1][wid] = srn; sm[2][wid] = scn; sm[3][wid] = fmx; sm[4][wid] = sab;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    DiagOut r{{0.0, 0.0, 0.0, 0.0, 0.0}};
+    for (int k = 0; k < kReduceThreads / 32; k++) {
+      r.v[0] += sm[0][k]; r.v[1] += sm[1][k]; r.v[2] += sm[2][k]; r.v[4] += sm[4][k];
+      r.v[3] = fmax(r.v[3], sm[3][k]);
+    }
+    partials[blockIdx.x] = r;
+  }
+}
+
+__global__ void k_nci_diag_final(const DiagOut *__restrict__ partials, int n, DiagOut *__restrict__ out) {
+  if (blockIdx.x != 0) return;
+  const int lane = threadIdx.x;
+  double a[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int k = lane; k < n; k += 32) {
+#pragma unroll
+    for (int j = 0; j < 5; j++) a[j] = j == 3 ? fmax(a[j], partials[k].v[j]) : a[j] + partials[k].v[j];
+  }
+#pragma unroll
+  for (int j = 0; j < 5; j++) a[j] = j == 3 ? warp_max(a[j]) : warp_sum(a[j]);
+  if (lane == 0) {
+    DiagOut r;
+#pragma unroll
+    for (int j = 0; j < 5; j++) r.v[j] = a[j];
+    *out = r;
+  }
+}
+
+cudaError_t launch_nci_diag(int dim, const KParams &P, const int32_t *phi, const float4 *frep, DiagOut *partials,
+                            DiagOut *out, cudaStream_t s) {
+  if (dim == 2)
+    k_nci_diag_partial<2><<<kReduceBlocks, kReduceThreads, 0, s>>>(P, phi, frep, partials);
+  else
+    k_nci_diag_partial<3><<<kReduceBlocks, kReduceThreads, 0, s>>>(P, phi, frep, partials);
+  k_nci_diag_final<<<1, 32, 0, s>>>(partials, kReduceBlocks, out);
+  return cudaGetLastError();
+}
+
 }  // namespace lbm

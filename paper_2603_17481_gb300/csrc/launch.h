@@ -59,4 +59,12 @@ cudaError_t launch_reduce(const KParams &P, const int32_t *phi, const float *u, 
 cudaError_t launch_reduce_n(const KParams &P, const int32_t *phi, const float *u, ReduceOut *partials,
                             int nblocks, ReduceOut *out, cudaStream_t s);
 
+// Near-contact film statistics (Sec. 3.3): over the cells with a partner (frep.w = 1 at gated
+// cells), V_film, sum |F_rep.n|, sum |F_cap.n|, max |F_rep|, sum |F_rep| in FP64, fixed order.
+struct DiagOut {
+  double v[5];
+};
+cudaError_t launch_nci_diag(int dim, const KParams &P, const int32_t *phi, const float4 *frep, DiagOut *partials,
+                            DiagOut *out, cudaStream_t s);
+
 }  // namespace lbm

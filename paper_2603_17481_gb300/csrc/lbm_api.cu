@@ -264,6 +264,7 @@ void lbm_destroy(lbm_ctx *c) {
   cudaFree(c->phi[0]); cudaFree(c->phi[1]);
   cudaFree(c->u); cudaFree(c->frep); cudaFree(c->nrm); cudaFree(c->mom); cudaFree(c->stage);
   cudaFree(c->partner); cudaFree(c->red_part); cudaFree(c->red_out);
+  cudaFree(c->diag_part); cudaFree(c->diag_out);
   cudaFree(c->tiles[0]); cudaFree(c->tiles[1]); cudaFree(c->ntiles);
   delete c;
 }
@@ -449,6 +450,40 @@ int lbm_read_nci(lbm_ctx *c, int32_t *partner, double *frep) {
     if ((rc = d2h(c, frep, c->stage, sizeof(double) * 3 * N))) return rc;
   }
   return sync(c);
+}
+
+int lbm_nci_diagnostics(lbm_ctx *c, double *out) {
+  if (!c || !out) return LBM_ERR_ARG;
+  if (!c->initialised) return LBM_ERR_STATE;
+  for (int k = 0; k < 7; k++) out[k] = 0.0;
+  if (!c->P.nci_on) return LBM_OK;
+  if (!c->diag_part) {
+    cudaError_t e = cudaMalloc(&c->diag_part, sizeof(DiagOut) * kReduceBlocks);
+    if (e == cudaSuccess) e = cudaMalloc(&c->diag_out, sizeof(DiagOut));
+    if (e != cudaSuccess) {
+      cudaFree(c->diag_part);
+      c->diag_part = nullptr;
+      c->diag_out = nullptr;
+      return from_cuda(e);
+    }
+  }
+  // the near-contact pass over the tiles listed for the current phi (the list stays for the next step)
+  int rc = from_cuda(timed(c, LBM_K_NCI, [&] {
+    return launch_nci(c->P.dim, c->K, c->T, c->phi[c->pcur], c->nrm, c->frep, nullptr, 0, c->tiles[c->pcur],
+                      c->ntiles + c->pcur, c->nci_blocks, c->stream);
+  }));
+  if (rc) return rc;
+  rc = from_cuda(timed(c, LBM_K_REDUCE, [&] {
+    return launch_nci_diag(c->P.dim, c->K, c->phi[c->pcur], c->frep, c->diag_part, c->diag_out, c->stream);
+  }));
+  if (rc) return rc;
+  DiagOut d;
+  if ((rc = d2h(c, &d, c->diag_out, sizeof(d)))) return rc;
+  if ((rc = sync(c))) return rc;
+  for (int k = 0; k < 5; k++) out[k] = d.v[k];
+  out[5] = d.v[2] > 0.0 ? d.v[1] / d.v[2] : 0.0;
+  out[6] = d.v[0] > 0.0 ? d.v[4] / d.v[0] : 0.0;
+  return LBM_OK;
 }
 
 int lbm_synchronize(lbm_ctx *c) {

@@ -1,0 +1,72 @@
+"""Near-contact film statistics (Sec. 3.3, Eq. 74) through the C ABI against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2603_17481_gb300 import binding as B
+from paper_2603_17481_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2603_17481_gb300 import build
+    build.build()
+    O.build()
+    torch.cuda.set_device(0)
+    return True
+
+
+def _pair(dim=3, **kw):
+    if dim == 3:
+        cfg = W.base_config(3, 48, 32, 32, 19, rho_g=0.1, **kw)
+        c = [(14.3, 15.6, 15.4), (33.1, 16.2, 15.7)]
+    else:
+        cfg = W.base_config(2, 96, 48, 1, 9, rho_g=0.1, **kw)
+        c = [(30.2, 23.6, 0.0), (65.9, 24.3, 0.0)]
+    phi, _ = W.droplet_fields(cfg, c, [8.0 if dim == 3 else 16.0] * 2, [(0, 0, 0)] * 2)
+    return cfg, W.to_q30_grid(phi)
+
+
+def _gpu_diag(cfg, phi):
+    sim = B.Lbm(cfg)
+    sim.init_fields(phi, np.zeros((3, phi.size)))
+    d = sim.nci_diagnostics()
+    part, _ = sim.read_nci()
+    sim.close()
+    return d, part
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_film_statistics_match_oracle(dim):
+    cfg, phi = _pair(dim)
+    P = O.make_params(cfg)
+    do = O.nci_diagnostics(P, phi)
+    dg, part_g = _gpu_diag(cfg, phi)
+    part_o, _, marg = O.nci(P, phi)
+    mis = np.any(part_g != part_o, axis=1)
+    assert np.all(marg[mis] < 1e-5)
+    assert do["V_film"] > 10
+    assert abs(dg["V_film"] - do["V_film"]) <= mis.sum()
+    if mis.sum() == 0:
+        for k in ("sum_rep_n", "sum_cap_n", "sum_rep", "R_n", "mean_rep"):
+            assert abs(dg[k] - do[k]) <= 2e-5 * abs(do[k]), (k, dg[k], do[k])
+        assert abs(dg["max_rep"] - do["max_rep"]) <= 2e-5 * do["max_rep"]
+
+
+def test_film_statistics_scale_and_vanish():
+    cfg, phi = _pair(3, A_rep=0.02, sigma=0.02)
+    d1, _ = _gpu_diag(cfg, phi)
+    d2, _ = _gpu_diag(_pair(3, A_rep=0.04, sigma=0.02)[0], phi)
+    d3, _ = _gpu_diag(_pair(3, A_rep=0.02, sigma=0.04)[0], phi)
+    assert d1["V_film"] == d2["V_film"] == d3["V_film"] > 0
+    assert abs(d2["R_n"] / d1["R_n"] - 2.0) < 1e-5 and abs(d3["R_n"] / d1["R_n"] - 0.5) < 1e-5
+    off, _ = _gpu_diag(dict(cfg, nci_on=0), phi)
+    assert all(v == 0.0 for v in off.values())
+    single = W.base_config(3, 40, 40, 40, 19)
+    ph1, _ = W.droplet_fields(single, [(19.7, 20.2, 19.9)], [12.0], [(0, 0, 0)])
+    iso, _ = _gpu_diag(single, W.to_q30_grid(ph1))
+    assert all(v == 0.0 for v in iso.values())
