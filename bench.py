@@ -556,6 +556,66 @@ def run_swarm(args, world, rank, local):
     }
 
 
+def run_selftune(args, world, rank, local):
+    """Film statistics over D x sigma x A_rep / sigma (Sec. 3.3): every case advanced in one batch,
+    lbm_nci_diagnostics every --diag-every steps, each case's record taken at its maximum film
+    volume (the instant of maximum activation)."""
+    import torch
+
+    from paper_2603_17481_gb300 import binding as B
+    from paper_2603_17481_gb300 import build as lbm_build
+    from paper_2603_17481_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    lbm_build.build()
+    cfgs = W.selftune_cases()
+    stream = torch.cuda.Stream()
+    sims = []
+    for cfg in cfgs:
+        phi, u = W.c4_fields(cfg)
+        s = B.Lbm(cfg, stream=stream.cuda_stream)
+        s.init_fields(phi, u)
+        sims.append(s)
+    cells = sum(s.N for s in sims)
+    batch = B.LbmBatch(sims, nstreams=16, stream=stream.cuda_stream)
+    best = [None] * len(sims)
+    every = args.diag_every + (args.diag_every & 1)
+    steps, ms = 0, 0.0
+    while steps < args.steps:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.step(every, sync=False)
+        e1.record(stream)
+        batch.synchronize()
+        ms += e0.elapsed_time(e1)
+        steps += every
+        for k, s in enumerate(sims):
+            d = s.nci_diagnostics()
+            if best[k] is None or d["V_film"] > best[k]["V_film"]:
+                best[k] = dict(d, step=steps)
+    batch.close()
+    for s in sims:
+        s.close()
+    if rank != 0:
+        return None
+    rows = []
+    for cfg, b in zip(cfgs, best):
+        rows.append({"D": cfg["diameter"], "sigma": cfg["sigma"], "A_rep_over_sigma": cfg["A_over_sigma"],
+                     "step": b["step"], "R_n": round(b["R_n"], 5), "max_Frep": b["max_rep"],
+                     "mean_Frep": b["mean_rep"], "V_film_over_D2": round(b["V_film"] / cfg["diameter"] ** 2, 5)})
+    mlups = cells * steps / (ms * 1e-3) / 1e6
+    return {
+        "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world, "steps": steps,
+        "warmup": 0, "ms_per_step": round(ms / steps, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "film statistics sweep: head-on collisions, D in {24,32,48}, sigma in "
+                               "{0.005,0.01,0.02}, A_rep/sigma in {0.5,1,2}, We=4.6, density ratio 10",
+                   "cases": len(cfgs), "cells": cells, "diag_every": every},
+        "gpu_launches": None,
+        "film_at_max_activation": rows,
+    }
+
+
 def run_reference(args, world, rank):
     """The FP64 CPU oracle as the reference arm, each step a bounded crop of the same workload."""
     if rank != 0:
@@ -621,14 +681,16 @@ def main():
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=120.0, help="seconds for the whole reference arm")
-    ap.add_argument("--workload", choices=["collision", "sweep", "swarm"], default="collision",
+    ap.add_argument("--workload", choices=["collision", "sweep", "swarm", "selftune"], default="collision",
                     help="collision: the 256x128x128 head-on case; sweep: the batched sweep of independent "
-                         "cases; swarm: the 512^3 bubble swarm with the near-contact repulsion on and off")
+                         "cases; swarm: the 512^3 bubble swarm with the near-contact repulsion on and off; "
+                         "selftune: film statistics over D x sigma x A_rep")
     ap.add_argument("--cases", type=int, default=512, help="sweep: number of cases")
     ap.add_argument("--streams", type=int, nargs="+", default=[16], help="sweep: graph branch counts to time")
     ap.add_argument("--swarm-L", type=int, default=512)
     ap.add_argument("--swarm-bubbles", type=int, default=1500)
     ap.add_argument("--swarm-steps", type=int, default=0, help="swarm: total steps before counting bubbles")
+    ap.add_argument("--diag-every", type=int, default=20, help="selftune: steps between film statistics")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
@@ -637,6 +699,8 @@ def main():
         line = run_sweep(args, world, rank, local)
     elif args.workload == "swarm":
         line = run_swarm(args, world, rank, local)
+    elif args.workload == "selftune":
+        line = run_selftune(args, world, rank, local)
     else:
         line = run_ours(args, world, rank, local)
     if rank == 0 and line is not None:

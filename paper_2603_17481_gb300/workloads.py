@@ -145,6 +145,32 @@ def c4_sweep(n=512, seed=17481, sigma=1e-3, we_min=1.0, we_max=100.0, grids=SWEE
     return out
 
 
+def selftune_cases(diameters=(24, 32, 48), sigmas=(0.005, 0.01, 0.02), ratios=(0.5, 1.0, 2.0), we=4.6):
+    """Head-on collisions over D x sigma x A_rep / sigma, for the film statistics of Sec. 3.3.
+
+    Each case is a periodic box (2D + 24) x (D + 16)^2 with two droplets of diameter D, 2R + 8 apart
+    along x, approaching at the relative speed U = sqrt(We sigma / (rho_l D)) with We = 4.6 (the
+    head-on experiment of Sec. 3.1); density ratio 10 and the other parameters as in the
+    collisions above. Fields come from ``c4_fields``. (The diameter is stored as ``diameter``: ``D``
+    is the phase-field mobility.)
+    """
+    out = []
+    for D in diameters:
+        for sg in sigmas:
+            for r in ratios:
+                R = D / 2.0
+                L, T = int(2 * D + 24), int(D + 16)
+                U = math.sqrt(we * sg / (1.0 * D))
+                cfg = base_config(3, L, T, T, 19, rho_g=0.1, sigma=sg, A_rep=r * sg)
+                c = (L - 1) / 2.0, (T - 1) / 2.0
+                sep = 2 * R + 8
+                cfg.update(R=R, diameter=float(D), weber=we, speed=U, A_over_sigma=r,
+                           centers=[(c[0] - sep / 2, c[1], c[1]), (c[0] + sep / 2, c[1], c[1])],
+                           velocities=[(U / 2, 0.0, 0.0), (-U / 2, 0.0, 0.0)])
+                out.append(cfg)
+    return out
+
+
 def c4_fields(cfg):
     """phi (rounded to the 2^-30 grid) and u of one sweep case."""
     phi, u = droplet_fields(cfg, cfg["centers"], [cfg["R"], cfg["R"]], cfg["velocities"])

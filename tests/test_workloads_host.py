@@ -70,3 +70,14 @@ def test_centroids_of_two_droplets():
     phi, _ = W.droplet_fields(cfg, [(24.0, 7.5, 5.5), (71.5, 7.5, 5.5)], [5.0, 5.0], [(0, 0, 0)] * 2)
     c = bench.centroids(cfg, phi)
     assert abs(c[0] - 24.0) < 1e-6 and abs(c[1] - 71.5) < 1e-6
+
+
+def test_workload_extras_do_not_shadow_parameters():
+    """Workload dictionaries carry extra keys (diameter, speed, ...) next to the model parameters:
+    none of them may overwrite a parameter such as the mobility D."""
+    import oracle as O
+    base = W.base_config(3, 8, 8, 8, 19)
+    for cfg in W.selftune_cases()[:3] + W.c4_sweep(3):
+        assert cfg["D"] == base["D"] and cfg["p"] == base["p"] and cfg["eps"] == base["eps"]
+        extra = set(cfg) - set(base)
+        assert not extra & set(O._FIELDS)
