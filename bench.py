@@ -28,7 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS & HBM-roofline fraction, FP32 vs FP16-store at stated φ error vs FP64"
-WORKLOAD = "3D head-on droplet collision 256x128x128 D3Q19, R=24, W=4, density ratio 100"
+WORKLOAD = "3D head-on droplet collision 256x128x128 D3Q{Q}, R=24, W=4, density ratio 100"
 HBM_FALLBACK_GBS = 6800.0
 # Algorithmic bytes per cell update (stored state only): populations read + written, phi read +
 # written, velocity written + read.
@@ -46,7 +46,7 @@ def hydro_bytes_per_cell(Q, pop_bytes):
 # a changed kernel reports null until it is profiled again.
 HYDRO_TRAFFIC = {
     # 337.48 MB read + 322.55 MB written (ncu --set full, one step launch of the 256x128x128 case)
-    ("f32", "ab69dab786068d1f"): 660.03e6,
+    ("f32", 19, "ab69dab786068d1f"): 660.03e6,
 }
 
 
@@ -173,9 +173,9 @@ def centroids(cfg, phi):
     return out
 
 
-def make_workload():
+def make_workload(Q=19):
     from paper_2603_17481_gb300 import workloads as W
-    cfg, phi, u = W.c3_head_on_3d()
+    cfg, phi, u = W.c3_head_on_3d(Q=Q)
     phi = W.to_q30_grid(phi)
     return cfg, phi, u
 
@@ -205,7 +205,7 @@ def run_ours(args, world, rank, local):
 
     torch.cuda.set_device(local)
     lbm_build.build()
-    cfg, phi, u = make_workload()
+    cfg, phi, u = make_workload(args.lattice)
     N = cfg["nx"] * cfg["ny"] * cfg["nz"]
     Q = cfg["Q"]
     stream = torch.cuda.Stream()
@@ -248,7 +248,7 @@ def run_ours(args, world, rank, local):
     hydro_avg = hydro_ms / max(hydro_n, 1)
     per_launch_bytes = hydro_bytes_per_cell(Q, pop_b) * N
     achieved = per_launch_bytes / (hydro_avg * 1e-3) / 1e9
-    key = (args.store, _src_hash("hydro_impl.cuh", "lbm_device.cuh"))
+    key = (args.store, Q, _src_hash("hydro_impl.cuh", "lbm_device.cuh"))
     traffic = HYDRO_TRAFFIC.get(key)
     gpu_launches = int(sum(n for k, (ms, n) in prof.items()))
 
@@ -339,7 +339,8 @@ def run_ours(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.store == "f32" else f"f32 ({args.store} store)",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": N, "lattice": "D3Q19 hydro, D3Q27 phase-field stencils",
+        "config": {"workload": WORKLOAD.format(Q=Q), "cells": N,
+                   "lattice": f"D3Q{Q} hydro, D3Q27 phase-field stencils",
                    "store": args.store, "near_contact": "on (w=3, q_th=0.125, eta=0.1, cos=-0.8)",
                    "l2": "inputs larger than L2 (2 x %.0f MB populations), no flush" % (Q * N * pop_b / 1e6),
                    "parallelism": f"{world} independent replica(s), one per GPU"},
@@ -625,7 +626,7 @@ def run_reference(args, world, rank):
     import oracle
     from paper_2603_17481_gb300 import workloads as W
     oracle.build()
-    cfg, phi, u = make_workload()
+    cfg, phi, u = make_workload(args.lattice)
     # calibrate: oracle throughput on a 64x32x32 crop of the workload
     budget = args.ref_budget / max(args.steps + args.warmup, 1)
 
@@ -662,7 +663,7 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": f"{nx}x{ny}x{nz} central crop per step"},
+        "config": {"workload": WORKLOAD.format(Q=args.lattice), "sample": f"{nx}x{ny}x{nz} central crop per step"},
         "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "value": round(v, 4), "unit": "MLUPS",
                          "sample": f"each step: one FP64 oracle step on a {nx}x{ny}x{nz} crop of the workload"},
         "e2e": {"value": round(v, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -676,6 +677,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--store", choices=["f32", "f16", "bf16"], default="f32")
+    ap.add_argument("--lattice", type=int, choices=[19, 27], default=19,
+                    help="collision: hydrodynamic lattice D3Q19 (the benchmark's) or D3Q27 (the paper's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", dest="variants", action="store_false")

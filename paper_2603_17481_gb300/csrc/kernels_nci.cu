@@ -125,24 +125,28 @@ k_nci_scan(const KParams P, const NciTable T, const int32_t *__restrict__ phi, c
     const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
     const bool inb = x < nx && y < ny && z < nz;
     const long long idx = inb ? (long long)x + (long long)nx * (y + (long long)ny * z) : 0;
-    const int32_t v = inb ? phi[idx] : 0;
-    const bool gated = inb && (q_gate_value(v) >= P.q_th);
-    if (!__syncthreads_or(gated)) {
-      if (debug && inb) {
-        frep[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (partner) partner[3 * idx] = partner[3 * idx + 1] = partner[3 * idx + 2] = INT32_MIN;
+    bool gated = false;
+    if (!tiles) {  // every tile is visited: skip those without an interfacial cell
+      gated = inb && (q_gate_value(phi[idx]) >= P.q_th);
+      if (!__syncthreads_or(gated)) {
+        if (debug && inb) {
+          frep[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (partner) partner[3 * idx] = partner[3 * idx + 1] = partner[3 * idx + 2] = INT32_MIN;
+        }
+        continue;  // uniform over the block
       }
-      continue;  // uniform over the block
     }
 
-    // stage phi of the tile + 3 halo (rows of HX = TX + 6 values): all rows' loads are issued
-    // before any is stored; the global row offsets and wrapped columns are kept for the normals
+    // Stage phi and the gated normals (written once per step by k_nci_normals) of the tile + 3
+    // halo, row by row (rows of HX = TX + 6 values): every row's phi loads are issued before any is
+    // stored; each warp then gates its own rows and loads the normals of their gated cells.
+    // Non-gated cells hold NaN normals, which fminf / fmaxf skip.
+    float lo0 = 1e30f, lo1 = 1e30f, lo2 = 1e30f, hi0 = -1e30f, hi1 = -1e30f, hi2 = -1e30f;
     {
       constexpr int NROWS = G::HY * G::HZ, RPW = (NROWS + G::NW - 1) / G::NW;
       const int xl = wrapn(x0 - G::H + tx, nx);
       const int xr = wrapn(x0 - G::H + 32 + (tx & 7), nx);
-      if (warp == 0) s_col[lane] = xl;
-      if (warp == 0 && lane < G::HX - 32) s_col[32 + lane] = xr;
+      const bool xtra = lane < G::HX - 32;
       int32_t va[RPW], vb[RPW];
 #pragma unroll
       for (int h = 0; h < RPW; h++) {
@@ -153,7 +157,7 @@ k_nci_scan(const KParams P, const NciTable T, const int32_t *__restrict__ phi, c
                                                  (long long)ny * (DIM == 3 ? wrapn(z0 + rz - G::H, nz) : 0));
           if (lane == 0) s_row[r] = row;
           va[h] = phi[row + xl];
-          if (lane < G::HX - 32) vb[h] = phi[row + xr];
+          if (xtra) vb[h] = phi[row + xr];
         }
       }
 #pragma unroll
@@ -161,34 +165,39 @@ k_nci_scan(const KParams P, const NciTable T, const int32_t *__restrict__ phi, c
         const int r = warp + h * G::NW;
         if (r < NROWS) {
           s_phi[r * G::HX + lane] = va[h];
-          if (lane < G::HX - 32) s_phi[r * G::HX + 32 + lane] = vb[h];
+          if (xtra) s_phi[r * G::HX + 32 + lane] = vb[h];
         }
       }
-    }
-    __syncthreads();
-    // gated normals of the box (written once per step by k_nci_normals), loads issued in batches
-    float lo0 = 1e30f, lo1 = 1e30f, lo2 = 1e30f, hi0 = -1e30f, hi1 = -1e30f, hi2 = -1e30f;
-    {
-      constexpr int BATCH = 2;
-      for (int t0 = tid; t0 < G::NB; t0 += BATCH * G::NT) {
-        float4 nb[BATCH];
-        bool gb[BATCH];
-#pragma unroll
-        for (int h = 0; h < BATCH; h++) {
-          const int b = t0 + h * G::NT;
-          gb[h] = b < G::NB && q_gate_value(s_phi[b]) >= P.q_th;
-          if (gb[h]) nb[h] = __ldg(nrm + s_row[b / G::HX] + s_col[b % G::HX]);
+      __syncwarp();  // this warp's rows of s_phi and s_row
+      const float qnan = __int_as_float(0x7fffffff);
+#pragma unroll 2
+      for (int h = 0; h < RPW; h++) {
+        const int r = warp + h * G::NW;
+        if (r >= NROWS) break;
+        const int b = r * G::HX + lane;
+        const bool ga = q_gate_value(s_phi[b]) >= P.q_th;
+        const bool gb = xtra && q_gate_value(s_phi[b + 32]) >= P.q_th;
+        float4 na, nb;
+        if (ga || gb) {
+          const long long row = s_row[r];
+          if (ga) na = __ldg(nrm + row + xl);
+          if (gb) nb = __ldg(nrm + row + xr);
         }
-#pragma unroll
-        for (int h = 0; h < BATCH; h++) {
-          const int b = t0 + h * G::NT;
-          if (!gb[h]) {
-            if (b < G::NB) s_n[b] = s_n[G::NB + b] = s_n[2 * G::NB + b] = __int_as_float(0x7fffffff);
-            continue;
+        if (ga) {
+          s_n[b] = na.x; s_n[G::NB + b] = na.y; s_n[2 * G::NB + b] = na.z;
+          lo0 = fminf(lo0, na.x); lo1 = fminf(lo1, na.y); lo2 = fminf(lo2, na.z);
+          hi0 = fmaxf(hi0, na.x); hi1 = fmaxf(hi1, na.y); hi2 = fmaxf(hi2, na.z);
+        } else {
+          s_n[b] = s_n[G::NB + b] = s_n[2 * G::NB + b] = qnan;
+        }
+        if (xtra) {
+          if (gb) {
+            s_n[b + 32] = nb.x; s_n[G::NB + b + 32] = nb.y; s_n[2 * G::NB + b + 32] = nb.z;
+            lo0 = fminf(lo0, nb.x); lo1 = fminf(lo1, nb.y); lo2 = fminf(lo2, nb.z);
+            hi0 = fmaxf(hi0, nb.x); hi1 = fmaxf(hi1, nb.y); hi2 = fmaxf(hi2, nb.z);
+          } else {
+            s_n[b + 32] = s_n[G::NB + b + 32] = s_n[2 * G::NB + b + 32] = qnan;
           }
-          s_n[b] = nb[h].x; s_n[G::NB + b] = nb[h].y; s_n[2 * G::NB + b] = nb[h].z;
-          lo0 = fminf(lo0, nb[h].x); lo1 = fminf(lo1, nb[h].y); lo2 = fminf(lo2, nb[h].z);
-          hi0 = fmaxf(hi0, nb[h].x); hi1 = fmaxf(hi1, nb[h].y); hi2 = fmaxf(hi2, nb[h].z);
         }
       }
     }
@@ -217,6 +226,7 @@ k_nci_scan(const KParams P, const NciTable T, const int32_t *__restrict__ phi, c
     const float rhi0 = s_rng[6 * G::NW + 3], rhi1 = s_rng[6 * G::NW + 4], rhi2 = s_rng[6 * G::NW + 5];
     const float thr = P.cos_opp + 1e-5f;
     const int ob0 = (DIM == 3 ? (tz + G::H) * G::HX * G::HY : 0) + (ty + G::H) * G::HX + tx + G::H;
+    if (tiles) gated = inb && q_gate_value(s_phi[ob0]) >= P.q_th;
     bool scan = false;
     if (gated) {
       const float n0 = s_n[ob0], n1 = s_n[G::NB + ob0], n2 = s_n[2 * G::NB + ob0];
