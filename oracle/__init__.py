@@ -92,6 +92,9 @@ def lib():
             L.orc_step.restype = ctypes.c_int
             L.orc_nci_diagnostics.argtypes = [_P, _D, _D]
             L.orc_nci_diagnostics.restype = ctypes.c_int
+            L.orc_curvature.argtypes = [_P, _D, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_longlong), _D]
+            L.orc_curvature.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -222,6 +225,19 @@ def nci_diagnostics(P: OrcParams, phi) -> dict:
     v, srn, scn, fmax, sabs = (float(x) for x in out)
     return {"V_film": v, "sum_rep_n": srn, "sum_cap_n": scn, "max_rep": fmax, "sum_rep": sabs,
             "R_n": srn / scn if scn > 0 else 0.0, "mean_rep": sabs / v if v > 0 else 0.0}
+
+
+def curvature(P: OrcParams, phi, kmin: float, kmax: float, nbins: int):
+    """Band cells, mean curvature and the histogram of kappa = div n (Eq. 78) on [kmin, kmax)."""
+    N = ncells(P)
+    phi = _f64(phi, (N,))
+    hist = np.zeros(nbins, dtype=np.int64)
+    out = np.zeros(2)
+    if lib().orc_curvature(ctypes.byref(P), _d(phi), float(kmin), float(kmax), int(nbins),
+                           hist.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), _d(out)):
+        raise MemoryError("oracle curvature failed")
+    n = float(out[0])
+    return {"band_cells": n, "mean": float(out[1]) / n if n > 0 else 0.0, "hist": hist}
 
 
 def phi_update(P: OrcParams, phi, u) -> np.ndarray:

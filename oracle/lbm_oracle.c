@@ -668,3 +668,52 @@ int orc_nci_diagnostics(const orc_params *P, const double *phi, double *out) {
   free(partner); free(frep); free(grad); free(lap);
   return 0;
 }
+
+/* Eq. 78: kappa = div n over the interfacial band, n from Eq. 57, divergence by Eq. 22. */
+int orc_curvature(const orc_params *P, const double *phi, double kmin, double kmax, int nbins, long long *hist,
+                  double *out) {
+  if (nbins < 1) return -1;
+  const long N = ncells(P);
+  double *grad = (double *)malloc(sizeof(double) * 3 * N);
+  double *nrm = (double *)malloc(sizeof(double) * 3 * N);
+  double *div = (double *)malloc(sizeof(double) * 3 * N);
+  if (!grad || !nrm || !div) {
+    free(grad); free(nrm); free(div);
+    return -1;
+  }
+  orc_grad_iso(P, phi, grad);
+  for (long n = 0; n < N; n++) {
+    double g2 = 0;
+    for (int a = 0; a < 3; a++) g2 += grad[a * N + n] * grad[a * N + n];
+    for (int a = 0; a < 3; a++) nrm[a * N + n] = grad[a * N + n] / (sqrt(g2) + P->eps_n);
+  }
+  /* div n = sum_a d_a n_a: the isotropic gradient of each component, then its own axis */
+  double *ga = (double *)malloc(sizeof(double) * 3 * N);
+  if (!ga) {
+    free(grad); free(nrm); free(div);
+    return -1;
+  }
+  for (int a = 0; a < 3; a++) {
+    orc_grad_iso(P, nrm + a * N, ga);
+    for (long n = 0; n < N; n++) div[a * N + n] = ga[a * N + n];
+  }
+  for (int k = 0; k < nbins; k++) hist[k] = 0;
+  double cnt = 0, sum = 0;
+  for (long n = 0; n < N; n++) {
+    /* the band gate, in binary32 under reading R13 like the near-contact gate */
+    const int band = P->decide_f32 ? (q_of_phi_f32(phi[n]) >= (float)P->q_th) : (q_of_phi(phi[n]) >= P->q_th);
+    if (!band) continue;
+    const double kap = div[n] + div[N + n] + div[2 * N + n];
+    cnt += 1.0;
+    sum += kap;
+    if (kap >= kmin && kap < kmax) {
+      int b = (int)((kap - kmin) / (kmax - kmin) * nbins);
+      if (b >= nbins) b = nbins - 1;
+      hist[b]++;
+    }
+  }
+  out[0] = cnt;
+  out[1] = sum;
+  free(grad); free(nrm); free(div); free(ga);
+  return 0;
+}

@@ -88,6 +88,15 @@ int orc_step(const orc_params *P, double *f, double *phi, int nsteps, double *u_
  * R_n = out[1] / out[2] and <|F_rep|>_film = out[4] / out[0]. Returns 0, or -1 on allocation failure. */
 int orc_nci_diagnostics(const orc_params *P, const double *phi, double *out);
 
+/* Interfacial mean curvature (Sec. 3.4, Eq. 78): kappa = div n with the outward unit normal
+ * n = grad(phi) / (|grad(phi)| + eps_n) of Eq. 57 (phi = 0 inside a bubble, 1 in the liquid), the
+ * divergence taken with the isotropic stencil of Eq. 22, at the cells of the interfacial band
+ * q >= q_th (Eq. 59). Histogram of kappa over nbins equal bins of [kmin, kmax) into hist (values
+ * outside are not binned); out[0] = number of band cells, out[1] = sum of kappa over the band.
+ * Returns 0, or -1 on allocation failure or nbins < 1. */
+int orc_curvature(const orc_params *P, const double *phi, double kmin, double kmax, int nbins, long long *hist,
+                  double *out);
+
 #ifdef __cplusplus
 }
 #endif
