@@ -460,8 +460,8 @@ def run_sweep(args, world, rank, local):
     }
 
 
-SWARM_WORKLOAD = ("3D buoyant bubble swarm, 512^3 periodic D3Q19, {nb} bubbles R ~ U[8,12] at seeded "
-                  "non-overlapping positions (gas fraction {gf:.3f}), W=4, density ratio 100, g=1e-6")
+SWARM_WORKLOAD = ("3D buoyant bubble swarm, {L}^3 periodic D3Q19, {nb} bubbles R ~ U[8,12] at seeded "
+                  "positions with surface gaps >= {gap} eps (gas fraction {gf:.3f}), W=4, density ratio 100, g=1e-6")
 
 
 def count_bubbles(gas):
@@ -499,7 +499,7 @@ def run_swarm(args, world, rank, local):
 
     torch.cuda.set_device(local)
     lbm_build.build()
-    cfg, cs, rs = W.c5_swarm(L=args.swarm_L, nb=args.swarm_bubbles, seed=17481 + rank)
+    cfg, cs, rs = W.c5_swarm(L=args.swarm_L, nb=args.swarm_bubbles, seed=17481 + rank, gap_eps=args.swarm_gap)
     phi, u = W.c5_fields(cfg, cs, rs)
     N = W.ncells(cfg)
     L = cfg["nx"]
@@ -526,15 +526,23 @@ def run_swarm(args, world, rank, local):
         prof = sim.profile_read()
         sim.profile(False)
         mlups, ms_max = whole_job_mlups(world, N, args.steps, e0.elapsed_time(e1), device=f"cuda:{local}")
-        rest = args.swarm_steps - args.warmup - args.steps
-        if rest > 0:
-            sim.step(rest)
+        done = args.warmup + args.steps
+        counts = {}
+        for mark in sorted(set(args.swarm_count_at) | {args.swarm_steps}):
+            if mark <= done:
+                continue
+            sim.step(mark - done)
+            done = mark
+            if mark != args.swarm_steps:
+                pm, _, _ = sim.read_fields(want=("phi",))
+                counts[str(mark)] = count_bubbles((pm < 0.5).reshape(L, L, L)) if np.all(np.isfinite(pm)) else None
         ph, _, _ = sim.read_fields(want=("phi",))
         m1, _ = sim.mass()
         runs[name] = {"value": round(mlups, 1), "ms_per_step": round(ms_max / args.steps, 5),
                       "kernels_ms_per_step": {k: round(ms / max(n, 1), 5) for k, (ms, n) in prof.items() if n},
                       "bubbles_after": count_bubbles((ph < 0.5).reshape(L, L, L)) if np.all(np.isfinite(ph)) else None,
                       "after_steps": max(args.swarm_steps, args.warmup + args.steps),
+                      "bubbles_at": counts,
                       "phi_mass_drift": abs(m1 - m0) / abs(m0)}
         sim.close()
     if rank != 0:
@@ -545,7 +553,8 @@ def run_swarm(args, world, rank, local):
         "metric": METRIC, "value": on, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": runs["nci_on"]["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": SWARM_WORKLOAD.format(nb=len(cs), gf=float((phi < 0.5).mean())), "cells": N,
+        "config": {"workload": SWARM_WORKLOAD.format(L=L, nb=len(cs), gap=args.swarm_gap, gf=float((phi < 0.5).mean())),
+                   "cells": N,
                    "l2": "inputs larger than L2, no flush",
                    "parallelism": f"{world} independent replica(s), one per GPU"},
         "step_roofline": {"bytes_per_cell": step_bytes_per_cell(19, 4),
@@ -693,6 +702,8 @@ def main():
     ap.add_argument("--swarm-L", type=int, default=512)
     ap.add_argument("--swarm-bubbles", type=int, default=1500)
     ap.add_argument("--swarm-steps", type=int, default=0, help="swarm: total steps before counting bubbles")
+    ap.add_argument("--swarm-count-at", type=int, nargs="*", default=[], help="swarm: also count bubbles at these steps")
+    ap.add_argument("--swarm-gap", type=float, default=2.0, help="swarm: minimum initial surface gap in units of eps")
     ap.add_argument("--diag-every", type=int, default=20, help="selftune: steps between film statistics")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)

@@ -30,13 +30,13 @@ def test_sweep_parameters():
 
 
 def test_swarm_fields_match_all_cells_profile():
-    cfg, cs, rs = W.c5_swarm(L=64, nb=12, seed=4)
-    assert len(cs) == 12
+    cfg, cs, rs = W.c5_swarm(L=80, nb=8, seed=4)
+    assert len(cs) == 8
     for i in range(len(cs)):
         for j in range(i):
             d = cs[i] - cs[j]
-            d -= 64 * np.round(d / 64)
-            assert np.linalg.norm(d) >= rs[i] + rs[j] + cfg["eps"]
+            d -= 80 * np.round(d / 80)
+            assert np.linalg.norm(d) >= rs[i] + rs[j] + 2 * cfg["eps"]
     phi, u = W.c5_fields(cfg, cs, rs)
     ref, _ = W.droplet_fields(cfg, cs, rs, [(0, 0, 0)] * len(cs), bubbles=True)
     # each truncated profile tail is below 1.2e-7, so the fields differ by less than that per bubble
