@@ -150,6 +150,16 @@ int lbm_read_nci(lbm_ctx *ctx, int32_t *partner, double *frep);
  * Allocates 24 KB of device scratch on the first call. Synchronises the context's stream. */
 int lbm_nci_diagnostics(lbm_ctx *ctx, double *out);
 
+/* Interfacial mean curvature of the current phi (Sec. 3.4, Eq. 78): kappa = div n with the outward
+ * unit normal n = grad(phi) / (|grad(phi)| + eps_n) (Eq. 57; phi = 0 inside a bubble), the
+ * divergence by the isotropic stencil of Eq. 22, at the cells of the band q >= q_th (Eq. 59).
+ * hist: nbins int64 counts of kappa over equal bins of [kmin, kmax) (values outside are not
+ * binned; nbins = 0 skips it and hist may be NULL); out[0] = band cells, out[1] = mean kappa.
+ * 0 <= nbins <= 4096 and kmax > kmin, else LBM_ERR_ARG. The normals of every cell are written to
+ * the near-contact normal buffer, which the next step recomputes where it reads it. Allocates
+ * 42 KB of device scratch on the first call; synchronises the context's stream. */
+int lbm_curvature(lbm_ctx *ctx, double kmin, double kmax, int nbins, int64_t *hist, double *out);
+
 /* Batches: independent contexts advanced together (a parameter sweep of uneven cases; no
  * counterpart in the paper, which runs one case at a time). One CUDA graph holds two steps of
  * every context, the contexts spread over nstreams concurrent branches, so that small cases fill

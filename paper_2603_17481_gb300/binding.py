@@ -73,6 +73,7 @@ def load():
     L.lbm_read_nci.argtypes = [_VP, _VP, _VP]
     L.lbm_mass_noalloc.argtypes = [_VP, _VP, _VP]
     L.lbm_nci_diagnostics.argtypes = [_VP, _VP]
+    L.lbm_curvature.argtypes = [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_int, _VP, _VP]
     L.lbm_batch_create.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.POINTER(_VP)]
     L.lbm_batch_step.argtypes = [_VP, ctypes.c_int]
     L.lbm_batch_synchronize.argtypes = [_VP]
@@ -89,7 +90,7 @@ def load():
     for name in ("lbm_create", "lbm_set_stream", "lbm_init_fields", "lbm_set_state", "lbm_get_state",
                  "lbm_step", "lbm_read_fields", "lbm_mass", "lbm_mass_noalloc", "lbm_read_nci", "lbm_synchronize",
                  "lbm_profile", "lbm_profile_read", "lbm_lattice", "lbm_batch_create", "lbm_batch_step",
-                 "lbm_nci_diagnostics",
+                 "lbm_nci_diagnostics", "lbm_curvature",
                  "lbm_batch_synchronize"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -233,6 +234,15 @@ def lbm_nci_diagnostics(ctx: int) -> dict:
     return dict(zip(DIAG_KEYS, (float(v) for v in out)))
 
 
+def lbm_curvature(ctx: int, kmin: float, kmax: float, nbins: int) -> dict:
+    hist = np.zeros(max(nbins, 0), dtype=np.int64)
+    out = np.zeros(2)
+    _check(load().lbm_curvature(_VP(ctx), float(kmin), float(kmax), int(nbins),
+                                hist.ctypes.data_as(_VP) if nbins > 0 else None, out.ctypes.data_as(_VP)),
+           "lbm_curvature")
+    return {"band_cells": float(out[0]), "mean": float(out[1]), "hist": hist}
+
+
 def lbm_synchronize(ctx: int) -> None:
     _check(load().lbm_synchronize(_VP(ctx)), "lbm_synchronize")
 
@@ -360,6 +370,9 @@ class Lbm:
 
     def nci_diagnostics(self):
         return lbm_nci_diagnostics(self.ctx)
+
+    def curvature(self, kmin: float, kmax: float, nbins: int):
+        return lbm_curvature(self.ctx, kmin, kmax, nbins)
 
     def profile(self, enable=True):
         lbm_profile(self.ctx, enable)

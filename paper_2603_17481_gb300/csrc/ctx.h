@@ -33,6 +33,8 @@ struct lbm_ctx {
   int nci_blocks = 0;
   lbm::ReduceOut *red_part = nullptr, *red_out = nullptr;
   lbm::DiagOut *diag_part = nullptr, *diag_out = nullptr;  // film statistics, on first use
+  unsigned long long *curv_hist = nullptr;  // curvature histogram (kMaxCurvBins), on first use
+  double *curv_part = nullptr;              // 2 per reduction block + 2 for the result
   int cur = 0;        // population buffer holding the current state
   int pcur = 0;       // phi buffer holding phi^n
   bool initialised = false;

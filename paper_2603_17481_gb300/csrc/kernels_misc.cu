@@ -363,4 +363,119 @@ cudaError_t launch_nci_diag(int dim, const KParams &P, const int32_t *phi, const
   return cudaGetLastError();
 }
 
+// Normals n = grad(phi) / (|grad(phi)| + eps_n) (Eqs. 22, 57) of every cell.
+template <int DIM>
+__global__ void __launch_bounds__(kReduceThreads)
+k_normals_all(const KParams P, const int32_t *__restrict__ phi, float4 *__restrict__ nrm) {
+  using SL = typename StencilOf<DIM>::type;
+  const int nx = P.nx, ny = P.ny, nz = P.nz;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < P.N; n += stride) {
+    const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long long)nx * ny));
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+#pragma unroll
+    for (int i = 1; i < SL::Q; i++) {
+      if (!positive<SL>(i)) continue;
+      const int c0 = SL::c(i, 0), c1 = SL::c(i, 1), c2 = SL::c(i, 2);
+      const long long ip = wrapn(x + c0, nx) + (long long)nx * (wrapn(y + c1, ny) + (long long)ny * wrapn(z + c2, nz));
+      const long long im = wrapn(x - c0, nx) + (long long)nx * (wrapn(y - c1, ny) + (long long)ny * wrapn(z - c2, nz));
+      const float d = SL::w(i) * dphi_of(phi[ip], phi[im]);
+      g0 += c0 * d;
+      g1 += c1 * d;
+      g2 += c2 * d;
+    }
+    g0 *= 3.0f; g1 *= 3.0f; g2 *= 3.0f;
+    const float inv = 1.0f / (sqrtf(g0 * g0 + g1 * g1 + g2 * g2) + P.eps_n);
+    nrm[n] = make_float4(g0 * inv, g1 * inv, g2 * inv, 0.0f);
+  }
+}
+
+// kappa = div n by the isotropic stencil (Eq. 22 on each component) at the band cells; a block
+// histogram in shared memory flushed with integer atomics, and the count and sum per block.
+template <int DIM>
+__global__ void __launch_bounds__(kReduceThreads)
+k_curv_partial(const KParams P, const int32_t *__restrict__ phi, const float4 *__restrict__ nrm, float kmin,
+               float kmax, int nbins, unsigned long long *__restrict__ hist, double *__restrict__ partials) {
+  using SL = typename StencilOf<DIM>::type;
+  __shared__ unsigned int sh[kMaxCurvBins];
+  for (int k = threadIdx.x; k < nbins; k += blockDim.x) sh[k] = 0u;
+  __syncthreads();
+  const int nx = P.nx, ny = P.ny, nz = P.nz;
+  const float scale = (float)nbins / (kmax - kmin);
+  double cnt = 0.0, sum = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < P.N; n += stride) {
+    if (!(q_gate_value(phi[n]) >= P.q_th)) continue;
+    const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long long)nx * ny));
+    float k = 0.f;
+#pragma unroll
+    for (int i = 1; i < SL::Q; i++) {
+      if (!positive<SL>(i)) continue;
+      const int c0 = SL::c(i, 0), c1 = SL::c(i, 1), c2 = SL::c(i, 2);
+      const long long ip = wrapn(x + c0, nx) + (long long)nx * (wrapn(y + c1, ny) + (long long)ny * wrapn(z + c2, nz));
+      const long long im = wrapn(x - c0, nx) + (long long)nx * (wrapn(y - c1, ny) + (long long)ny * wrapn(z - c2, nz));
+      const float4 a = nrm[ip], b = nrm[im];
+      k += SL::w(i) * (c0 * (a.x - b.x) + c1 * (a.y - b.y) + c2 * (a.z - b.z));
+    }
+    k *= 3.0f;
+    cnt += 1.0;
+    sum += (double)k;
+    if (k >= kmin && k < kmax) {
+      int bin = (int)((k - kmin) * scale);
+      bin = bin < nbins ? bin : nbins - 1;
+      atomicAdd(&sh[bin], 1u);
+    }
+  }
+  __shared__ double sm[2][kReduceThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  cnt = warp_sum(cnt);
+  sum = warp_sum(sum);
+  if (lane == 0) {
+    sm[0][wid] = cnt;
+    sm[1][wid] = sum;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double c = 0.0, t = 0.0;
+    for (int w = 0; w < kReduceThreads / 32; w++) {
+      c += sm[0][w];
+      t += sm[1][w];
+    }
+    partials[2 * blockIdx.x] = c;
+    partials[2 * blockIdx.x + 1] = t;
+  }
+  for (int k = threadIdx.x; k < nbins; k += blockDim.x)
+    if (sh[k]) atomicAdd(&hist[k], (unsigned long long)sh[k]);
+}
+
+__global__ void k_curv_final(const double *__restrict__ partials, int n, double *__restrict__ out) {
+  if (blockIdx.x != 0) return;
+  double c = 0.0, t = 0.0;
+  for (int k = threadIdx.x; k < n; k += 32) {
+    c += partials[2 * k];
+    t += partials[2 * k + 1];
+  }
+  c = warp_sum(c);
+  t = warp_sum(t);
+  if (threadIdx.x == 0) {
+    out[0] = c;
+    out[1] = t;
+  }
+}
+
+cudaError_t launch_curvature(int dim, const KParams &P, const int32_t *phi, float4 *nrm, float kmin, float kmax,
+                             int nbins, unsigned long long *hist, double *partials, double *out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * nbins, s);
+  if (e != cudaSuccess) return e;
+  if (dim == 2) {
+    k_normals_all<2><<<kReduceBlocks, kReduceThreads, 0, s>>>(P, phi, nrm);
+    k_curv_partial<2><<<kReduceBlocks, kReduceThreads, 0, s>>>(P, phi, nrm, kmin, kmax, nbins, hist, partials);
+  } else {
+    k_normals_all<3><<<kReduceBlocks, kReduceThreads, 0, s>>>(P, phi, nrm);
+    k_curv_partial<3><<<kReduceBlocks, kReduceThreads, 0, s>>>(P, phi, nrm, kmin, kmax, nbins, hist, partials);
+  }
+  k_curv_final<<<1, 32, 0, s>>>(partials, kReduceBlocks, out);
+  return cudaGetLastError();
+}
+
 }  // namespace lbm

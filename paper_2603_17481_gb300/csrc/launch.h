@@ -67,4 +67,11 @@ struct DiagOut {
 cudaError_t launch_nci_diag(int dim, const KParams &P, const int32_t *phi, const float4 *frep, DiagOut *partials,
                             DiagOut *out, cudaStream_t s);
 
+// Interfacial mean curvature kappa = div n (Sec. 3.4, Eq. 78): normals of every cell into nrm, then
+// over the band q >= q_th a histogram of kappa on [kmin, kmax) (nbins <= kMaxCurvBins, integer
+// counts) and the band's cell count and sum of kappa (FP64, fixed order): out = {count, sum}.
+constexpr int kMaxCurvBins = 4096;
+cudaError_t launch_curvature(int dim, const KParams &P, const int32_t *phi, float4 *nrm, float kmin, float kmax,
+                             int nbins, unsigned long long *hist, double *partials, double *out, cudaStream_t s);
+
 }  // namespace lbm

@@ -265,6 +265,7 @@ void lbm_destroy(lbm_ctx *c) {
   cudaFree(c->u); cudaFree(c->frep); cudaFree(c->nrm); cudaFree(c->mom); cudaFree(c->stage);
   cudaFree(c->partner); cudaFree(c->red_part); cudaFree(c->red_out);
   cudaFree(c->diag_part); cudaFree(c->diag_out);
+  cudaFree(c->curv_hist); cudaFree(c->curv_part);
   cudaFree(c->tiles[0]); cudaFree(c->tiles[1]); cudaFree(c->ntiles);
   delete c;
 }
@@ -483,6 +484,35 @@ int lbm_nci_diagnostics(lbm_ctx *c, double *out) {
   for (int k = 0; k < 5; k++) out[k] = d.v[k];
   out[5] = d.v[2] > 0.0 ? d.v[1] / d.v[2] : 0.0;
   out[6] = d.v[0] > 0.0 ? d.v[4] / d.v[0] : 0.0;
+  return LBM_OK;
+}
+
+int lbm_curvature(lbm_ctx *c, double kmin, double kmax, int nbins, int64_t *hist, double *out) {
+  if (!c || !out || (nbins > 0 && !hist)) return LBM_ERR_ARG;
+  if (nbins < 0 || nbins > kMaxCurvBins || !(kmax > kmin)) return LBM_ERR_ARG;
+  if (!c->initialised) return LBM_ERR_STATE;
+  if (!c->curv_hist) {
+    cudaError_t e = cudaMalloc(&c->curv_hist, sizeof(unsigned long long) * kMaxCurvBins);
+    if (e == cudaSuccess) e = cudaMalloc(&c->curv_part, sizeof(double) * (2 * kReduceBlocks + 2));
+    if (e != cudaSuccess) {
+      cudaFree(c->curv_hist);
+      c->curv_hist = nullptr;
+      c->curv_part = nullptr;
+      return from_cuda(e);
+    }
+  }
+  double *res = c->curv_part + 2 * kReduceBlocks;
+  int rc = from_cuda(timed(c, LBM_K_REDUCE, [&] {
+    return launch_curvature(c->P.dim, c->K, c->phi[c->pcur], c->nrm, (float)kmin, (float)kmax, nbins > 0 ? nbins : 1,
+                            c->curv_hist, c->curv_part, res, c->stream);
+  }));
+  if (rc) return rc;
+  double r[2];
+  if ((rc = d2h(c, r, res, sizeof(r)))) return rc;
+  if (nbins > 0 && (rc = d2h(c, hist, c->curv_hist, sizeof(int64_t) * nbins))) return rc;
+  if ((rc = sync(c))) return rc;
+  out[0] = r[0];
+  out[1] = r[0] > 0.0 ? r[1] / r[0] : 0.0;
   return LBM_OK;
 }
 

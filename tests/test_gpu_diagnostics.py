@@ -70,3 +70,28 @@ def test_film_statistics_scale_and_vanish():
     ph1, _ = W.droplet_fields(single, [(19.7, 20.2, 19.9)], [12.0], [(0, 0, 0)])
     iso, _ = _gpu_diag(single, W.to_q30_grid(ph1))
     assert all(v == 0.0 for v in iso.values())
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_curvature_matches_oracle(dim):
+    """Interfacial mean curvature (Eq. 78) of a few bubbles: band cells identical, mean within 1e-4,
+    and histogram counts differing only where a value sits within FP32 rounding of a bin edge."""
+    if dim == 3:
+        cfg = W.base_config(3, 64, 48, 40, 19)
+        c, R = [(16.3, 20.1, 19.6), (44.7, 27.2, 21.3)], [9.0, 12.0]
+        lo, hi, nb = 0.0, 0.5, 100
+    else:
+        cfg = W.base_config(2, 128, 96, 1, 9)
+        c, R = [(40.2, 45.3, 0.0), (90.6, 50.1, 0.0)], [14.0, 20.0]
+        lo, hi, nb = 0.0, 0.25, 100
+    phi, _ = W.droplet_fields(cfg, c, R, [(0, 0, 0)] * 2, bubbles=True)
+    phi = W.to_q30_grid(phi)
+    ko = O.curvature(O.make_params(cfg), phi, lo, hi, nb)
+    sim = B.Lbm(cfg)
+    sim.init_fields(phi, np.zeros((3, phi.size)))
+    kg = sim.curvature(lo, hi, nb)
+    sim.close()
+    assert kg["band_cells"] == ko["band_cells"] > 100
+    assert abs(kg["mean"] - ko["mean"]) <= 1e-4 * abs(ko["mean"])
+    assert abs(int(kg["hist"].sum()) - int(ko["hist"].sum())) <= 2
+    assert np.abs(kg["hist"] - ko["hist"]).sum() <= max(4, 0.002 * ko["hist"].sum())
