@@ -464,8 +464,10 @@ SWARM_WORKLOAD = ("3D buoyant bubble swarm, {L}^3 periodic D3Q19, {nb} bubbles R
                   "positions with surface gaps >= {gap} eps (gas fraction {gf:.3f}), W=4, density ratio 100, g=1e-6")
 
 
-def count_bubbles(gas):
-    """Connected components (6-neighbour) of a boolean (nz, ny, nx) mask on a periodic grid."""
+def count_bubbles(gas, volumes=False):
+    """Connected components (6-neighbour) of a boolean (nz, ny, nx) mask on a periodic grid; with
+    ``volumes`` also the cell count of each component."""
+    import numpy as np
     from scipy import ndimage
     lab, n = ndimage.label(gas)
     parent = list(range(n + 1))
@@ -484,7 +486,14 @@ def count_bubbles(gas):
             ri, rj = find(i), find(j)
             if ri != rj:
                 parent[max(ri, rj)] = min(ri, rj)
-    return len({find(i) for i in range(1, n + 1)})
+    roots = [find(i) for i in range(1, n + 1)]
+    if not volumes:
+        return len(set(roots))
+    sizes = np.bincount(lab.ravel(), minlength=n + 1)[1:]
+    vol = {}
+    for r, v in zip(roots, sizes.tolist()):
+        vol[r] = vol.get(r, 0) + v
+    return len(vol), sorted(vol.values())
 
 
 def run_swarm(args, world, rank, local):
@@ -538,11 +547,21 @@ def run_swarm(args, world, rank, local):
                 counts[str(mark)] = count_bubbles((pm < 0.5).reshape(L, L, L)) if np.all(np.isfinite(pm)) else None
         ph, _, _ = sim.read_fields(want=("phi",))
         m1, _ = sim.mass()
+        kap = sim.curvature(0.0, 0.5, 50)  # kappa = div n, Eq. 78: 2 / R for R in [8, 12] is 0.17-0.25
+        deq = None
+        if np.all(np.isfinite(ph)):
+            _, vols = count_bubbles((ph < 0.5).reshape(L, L, L), volumes=True)
+            d = (6.0 * np.asarray(vols, dtype=np.float64) / np.pi) ** (1.0 / 3.0)
+            deq = {"mean": round(float(d.mean()), 3), "std": round(float(d.std()), 3),
+                   "hist_1lu_0_40": np.histogram(d, bins=40, range=(0, 40))[0].tolist()}
         runs[name] = {"value": round(mlups, 1), "ms_per_step": round(ms_max / args.steps, 5),
                       "kernels_ms_per_step": {k: round(ms / max(n, 1), 5) for k, (ms, n) in prof.items() if n},
                       "bubbles_after": count_bubbles((ph < 0.5).reshape(L, L, L)) if np.all(np.isfinite(ph)) else None,
                       "after_steps": max(args.swarm_steps, args.warmup + args.steps),
                       "bubbles_at": counts,
+                      "kappa": {"mean": round(kap["mean"], 5), "band_cells": kap["band_cells"],
+                                "hist_0_0.5_50": kap["hist"].tolist()},
+                      "D_eq": deq,
                       "phi_mass_drift": abs(m1 - m0) / abs(m0)}
         sim.close()
     if rank != 0:

@@ -55,13 +55,19 @@ def test_count_bubbles_periodic():
     assert bench.count_bubbles(g) == 4
     g[5, 5, 5] = True
     assert bench.count_bubbles(g) == 5
+    n, vols = bench.count_bubbles(g, volumes=True)
+    assert n == 5 and sorted(vols) == [1, 2, 2, 2, 2]
     assert bench.count_bubbles(np.zeros((4, 4, 4), bool)) == 0
 
 
 def test_count_bubbles_of_generated_swarm():
     cfg, cs, rs = W.c5_swarm(L=96, nb=20, seed=9)
     phi, _ = W.c5_fields(cfg, cs, rs)
-    assert bench.count_bubbles((phi < 0.5).reshape(96, 96, 96)) == len(cs)
+    n, vols = bench.count_bubbles((phi < 0.5).reshape(96, 96, 96), volumes=True)
+    assert n == len(cs) == len(vols)
+    # each component's volume is its sphere's to within the lattice sampling of the surface
+    exp = sorted(4.0 / 3.0 * np.pi * rs ** 3)
+    assert np.all(np.abs(np.asarray(vols) - exp) < 0.05 * np.asarray(exp))
 
 
 def test_centroids_of_two_droplets():
