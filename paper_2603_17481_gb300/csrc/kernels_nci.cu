@@ -37,6 +37,24 @@ template <int DIM> struct NciGeom {
                                  sizeof(int) * HX + sizeof(__half) * 6 * ((DIM == 3 ? NZR : 0) + NYR);
 };
 
+// The eight windows [o, o + 6], o = 0..7, of fourteen values: the suffix extremes of [0, 6] and the
+// prefix extremes of [7, 13] (van Herk / Gil-Werman), 18 operations instead of 48.
+template <bool MAX>
+__device__ __forceinline__ void win7x8(const float *v, float *out) {
+  auto op = [](float a, float b) { return MAX ? fmaxf(a, b) : fminf(a, b); };
+  float suf[7], pre[7];
+  suf[6] = v[6];
+#pragma unroll
+  for (int i = 5; i >= 0; i--) suf[i] = op(v[i], suf[i + 1]);
+  pre[0] = v[7];
+#pragma unroll
+  for (int j = 1; j < 7; j++) pre[j] = op(pre[j - 1], v[7 + j]);
+  out[0] = suf[0];
+#pragma unroll
+  for (int o = 1; o < 7; o++) out[o] = op(suf[o], pre[o - 1]);
+  out[7] = pre[6];
+}
+
 // The four windows [o, o + 6], o = 0..3, of ten values share the core [3, 6] and the pairs (1, 2)
 // and (7, 8): 13 min (or max) operations instead of 24.
 template <bool MAX>
@@ -97,7 +115,7 @@ k_nci_normals(const KParams P, const int32_t *__restrict__ phi, float4 *__restri
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(NciGeom<DIM>::NT, 2)
+__global__ void __launch_bounds__(NciGeom<DIM>::NT, NciGeom<DIM>::NT >= 1024 ? 1 : 2)
 k_nci_scan(const KParams P, const NciTable T, const int32_t *__restrict__ phi, const float4 *__restrict__ nrm,
            float4 *__restrict__ frep, int32_t *__restrict__ partner, int debug, const int *__restrict__ tiles,
            const int *__restrict__ ntiles, int total, int gtx, int gty) {
@@ -270,6 +288,12 @@ k_nci_scan(const KParams P, const NciTable T, const int32_t *__restrict__ phi, c
           if constexpr (G::HY == 10 && G::TY == 4) {
             float r[4];
             if (c & 1) win7x4<true>(v, r); else win7x4<false>(v, r);
+#pragma unroll
+            for (int o = 0; o < G::TY; o++)
+              s_yr[c * G::NYR + (cz * G::TY + o) * G::HX + cx] = (c & 1) ? __float2half_ru(r[o]) : __float2half_rd(r[o]);
+          } else if constexpr (G::HY == 14 && G::TY == 8) {
+            float r[8];
+            if (c & 1) win7x8<true>(v, r); else win7x8<false>(v, r);
 #pragma unroll
             for (int o = 0; o < G::TY; o++)
               s_yr[c * G::NYR + (cz * G::TY + o) * G::HX + cx] = (c & 1) ? __float2half_ru(r[o]) : __float2half_rd(r[o]);

@@ -248,7 +248,10 @@ struct Phase3 {
   static constexpr int QX = TX + 2, QY = TY + 2, NQ = QX * QY;  // PSXY / a planes (halo 1)
   static constexpr int NC = TX * TY;
   static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
-  static constexpr int NFLG = (ZC / 4) * (TY / 4);
+  // near-contact tiles (NY x NZ in y, z) of the block's column: flags per z chunk of the march
+  static constexpr int NY = NciTile<3>::Y, NZ = NciTile<3>::Z, FY = TY / NY;
+  static_assert(TY % NY == 0 && ZC % NZ == 0 && NZ == 4, "near-contact tiles nest in the march blocks");
+  static constexpr int NFLG = (ZC / NZ) * FY;
   static constexpr size_t smem = sizeof(float) * (2 * NP + 4 * NQ) + sizeof(int32_t) * 4 * NP +
                                  sizeof(float) * 4 * NP +
                                  sizeof(float) * (12 * NQ + 2 * NQ + 2 * NC + QX * TY + TX * QY + 2 * NC) +
@@ -499,15 +502,15 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
         acc += TZF[(k & 1) * G::NC + tid] - TZF[((k + 1) & 1) * G::NC + tid];
         const int32_t vn = PH[s4k * G::NP + G::pi(lx, ly)] + acc;
         phi_out[(long long)x + (long long)nx * (y + (long long)ny * k)] = vn;
-        if (tiles && q_gate_value(vn) >= P.q_th) FLG[((k - zb) >> 2) * (G::TY / 4) + (ly >> 2)] = 1;
+        if (tiles && q_gate_value(vn) >= P.q_th) FLG[((k - zb) / G::NZ) * G::FY + ly / G::NY] = 1;
       }
     }
   }
   if (tiles) {
     __syncthreads();
     if (tid < G::NFLG && FLG[tid]) {
-      const int gtx = (nx + 31) / 32, gty = (ny + 3) / 4;
-      const int bzt = zb / 4 + tid / (G::TY / 4), byt = y0 / 4 + tid % (G::TY / 4);
+      const int gtx = (nx + 31) / 32, gty = (ny + G::NY - 1) / G::NY;
+      const int bzt = zb / G::NZ + tid / G::FY, byt = y0 / G::NY + tid % G::FY;
       tiles[atomicAdd(ntiles, 1)] = blockIdx.x + gtx * (byt + gty * bzt);
     }
   }

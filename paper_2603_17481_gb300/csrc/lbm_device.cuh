@@ -165,7 +165,7 @@ template <> struct Tile<3> { static constexpr int X = 32, Y = 4, Z = 2; };
 
 template <int DIM> struct NciTile;
 template <> struct NciTile<2> { static constexpr int X = 32, Y = 16, Z = 1; };
-template <> struct NciTile<3> { static constexpr int X = 32, Y = 4, Z = 4; };
+template <> struct NciTile<3> { static constexpr int X = 32, Y = 8, Z = 4; };
 
 // The phase-field kernel lists near-contact tiles, so both use the same tiling.
 template <int DIM> struct PhaseTile : NciTile<DIM> {};
