@@ -245,9 +245,11 @@ k_phase(const KParams P, const int32_t *__restrict__ phi, const float *__restric
 struct Phase3 {
   static constexpr int TX = 32, TY = 8, ZC = 16, NT = TX * TY;  // ZC: the largest z chunk
   static constexpr int PX = TX + 4, PY = TY + 4, NP = PX * PY;  // phi / RZ planes (halo 2)
-  static constexpr int QX = TX + 2, QY = TY + 2, NQ = QX * QY;  // PSXY / a planes (halo 1)
+  // PSXY / a planes (halo 1): TX + 2 columns used, stored with the pitch of the phi planes so that
+  // a warp's consecutive entries are consecutive words (no bank conflicts) and pi() = qi() + PX + 1
+  static constexpr int QW = TX + 2, QX = PX, QY = TY + 2, NQ = QX * QY;
   static constexpr int NC = TX * TY;
-  static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
+  static constexpr int NFX = PX * TY, NFY = TX * (TY + 1);  // x faces at pitch PX (TX + 1 used)
   // near-contact tiles (NY x NZ in y, z) of the block's column: flags per z chunk of the march
   static constexpr int NY = NciTile<3>::Y, NZ = NciTile<3>::Z, FY = TY / NY;
   static_assert(TY % NY == 0 && ZC % NZ == 0 && NZ == 4, "near-contact tiles nest in the march blocks");
@@ -281,7 +283,7 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
   float *AXZ = A + 12 * G::NQ;                               // [NQ]
   float *AYZ = AXZ + G::NQ;                                  // [NQ]
   float *ASXY = AYZ + G::NQ;                                 // [2][NC]
-  float *UX = ASXY + 2 * G::NC;                              // [TY][QX]: lx -1..32
+  float *UX = ASXY + 2 * G::NC;                              // [TY][QX]: lx -1..32 at columns 0..33
   float *UY = UX + G::QX * G::TY;                            // [QY][TX]: ly -1..TY
   float *UZ = UY + G::TX * G::QY;                            // [2][NC]
   int32_t *TXF = reinterpret_cast<int32_t *>(UZ + 2 * G::NC);  // [TY][TX+1]
@@ -315,13 +317,14 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
   // shared-memory index of the halo-1 entries t = tid and tid + NT, and of the x faces t = tid and
   // tid + NT as (plane index, row): also constant over the march
   static_assert(G::NQ <= 2 * G::NT && G::NFX <= 2 * G::NT && G::NFY <= 2 * G::NT, "two entries per thread");
-  int cq[2], cfx[2], lfx[2];
+  // which of this thread's entries t = tid and tid + NT are used columns (entry t of a halo-1 plane
+  // is the cell at phi-plane index t + PX + 1; x face t lies left of the cell at t + 2 PX + 1)
+  bool vq[2], vfx[2];
 #pragma unroll
   for (int h = 0; h < 2; h++) {
     const int t = tid + h * G::NT;
-    cq[h] = G::pi(t % G::QX - 1, t / G::QX - 1);
-    lfx[h] = t / (G::TX + 1);
-    cfx[h] = G::pi(t % (G::TX + 1) - 1, lfx[h]);
+    vq[h] = t < G::NQ && t % G::QX < G::QW;
+    vfx[h] = t < G::NFX && t % G::PX < G::TX + 1;
   }
   if (tid < G::NFLG) FLG[tid] = 0;
 
@@ -389,8 +392,8 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
 #pragma unroll
       for (int h = 0; h < 2; h++) {
         const int t = tid + h * G::NT;
-        if (t >= G::NQ) break;
-        const int c = cq[h];
+        if (!vq[h]) continue;
+        const int c = t + G::PX + 1;
         const float r0 = s141(p2[c - G::PX - 1], p2[c - G::PX], p2[c - G::PX + 1]);
         const float r1 = s141(p2[c - 1], p2[c], p2[c + 1]);
         const float r2 = s141(p2[c + G::PX - 1], p2[c + G::PX], p2[c + G::PX + 1]);
@@ -408,8 +411,8 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
 #pragma unroll
       for (int h = 0; h < 2; h++) {
         const int t = tid + h * G::NT;
-        if (t >= G::NQ) break;
-        const int c = cq[h];
+        if (!vq[h]) continue;
+        const int c = t + G::PX + 1;
         const float g0 = gs * s141(rz[c - G::PX + 1] - rz[c - G::PX - 1], rz[c + 1] - rz[c - 1],
                                    rz[c + G::PX + 1] - rz[c + G::PX - 1]);
         const float g1 = gs * s141(rz[c + G::PX - 1] - rz[c - G::PX - 1], rz[c + G::PX] - rz[c - G::PX],
@@ -439,7 +442,10 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
       }
       if (k >= zb) {
         const float *am = A + s4km * 3 * G::NQ, *a0 = A + s4k * 3 * G::NQ, *ap = A + s4k1 * 3 * G::NQ;
-        for (int t = tid; t < G::NQ; t += G::NT) {
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          const int t = tid + h * G::NT;
+          if (!vq[h]) continue;
           AXZ[t] = s141(am[t], a0[t], ap[t]);
           AYZ[t] = s141(am[G::NQ + t], a0[G::NQ + t], ap[G::NQ + t]);
         }
@@ -454,16 +460,15 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
 #pragma unroll
         for (int h = 0; h < 2; h++) {
           const int t = tid + h * G::NT;
-          if (t >= G::NFX) break;
-          const int c = cfx[h], ly = lfx[h];
-          const int lx = c - G::pi(0, ly);
+          if (!vfx[h]) continue;
+          const int c = t + 2 * G::PX + 1;  // the cell left of the face
           const float di = s141(rz[c - G::PX] - rz[c - G::PX + 1], rz[c] - rz[c + 1],
                                 rz[c + G::PX] - rz[c + G::PX + 1]);
-          const int q = G::qi(lx, ly);
+          const int q = t + G::QX;
           const float cs = s141(AXZ[q - G::QX] + AXZ[q - G::QX + 1], AXZ[q] + AXZ[q + 1],
                                 AXZ[q + G::QX] + AXZ[q + G::QX + 1]);
           const float vm = p0[c - 1], v0 = p0[c], v1 = p0[c + 1], vp = p0[c + 2];
-          const float uf = 0.5f * (UX[ly * G::QX + lx + 1] + UX[ly * G::QX + lx + 2]);
+          const float uf = 0.5f * (UX[t] + UX[t + 1]);
           const float up = uf >= 0.0f ? v0 + 0.5f * minmod_f(v0 - vm, v1 - v0) : v1 - 0.5f * minmod_f(v1 - v0, vp - v1);
           TXF[t] = __float2int_rn(kQ30 * fmaf(Dx, di, fmaf(k3s, cs, uf * up)));
         }
@@ -497,7 +502,7 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
       const int lx = tid & 31, ly = tid >> 5;
       const int x = x0 + lx, y = y0 + ly;
       if (x < nx && y < ny) {
-        int32_t acc = TXF[ly * (G::TX + 1) + lx] - TXF[ly * (G::TX + 1) + lx + 1];
+        int32_t acc = TXF[ly * G::PX + lx] - TXF[ly * G::PX + lx + 1];
         acc += TYF[ly * G::TX + lx] - TYF[(ly + 1) * G::TX + lx];
         acc += TZF[(k & 1) * G::NC + tid] - TZF[((k + 1) & 1) * G::NC + tid];
         const int32_t vn = PH[s4k * G::NP + G::pi(lx, ly)] + acc;
