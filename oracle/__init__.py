@@ -240,6 +240,35 @@ def curvature(P: OrcParams, phi, kmin: float, kmax: float, nbins: int):
     return {"band_cells": n, "mean": float(out[1]) / n if n > 0 else 0.0, "hist": hist}
 
 
+def energy_spectrum(P: OrcParams, phi, u, nshells: int) -> np.ndarray:
+    """Carrier-phase kinetic-energy spectrum (Sec. 3.4), numpy FFT as the transform.
+
+    The carrier phase is the liquid, chi = 1 where phi >= 1/2 (reading R23). The fluctuation is
+    u' = chi (u - <u>_liquid) and u_hat(k) = (1/N) sum_x u'(x) exp(-i k.x) per component, so that
+    sum_k |u_hat|^2 = <|u'|^2> (Parseval). With k_a = 2 pi m_a / n_a and the shell width
+    2 pi / max(n_a), E(K) = sum over k with round(|k| / width) = K of |u_hat(k)|^2 / 2.
+    Returns E for K = 0 .. nshells - 1 (energy beyond the last shell is not returned).
+    """
+    nx, ny, nz = P.nx, P.ny, P.nz
+    N = nx * ny * nz
+    phi = _f64(phi, (N,))
+    u = _f64(u, (3, N))
+    chi = (phi >= 0.5).astype(np.float64)
+    ubar = (u * chi).sum(axis=1) / max(chi.sum(), 1.0)
+    up = chi * (u - ubar[:, None])
+    m = [np.fft.fftfreq(n, 1.0 / n) for n in (nz, ny, nx)]
+    kk = np.sqrt(sum((2 * np.pi * mm / n)[tuple(slice(None) if i == j else None for j in range(3))] ** 2
+                     for i, (mm, n) in enumerate(zip(m, (nz, ny, nx)))))
+    shell = np.rint(kk / (2 * np.pi / max(nx, ny, nz))).astype(np.int64)
+    E = np.zeros(nshells)
+    for a in range(3):
+        uh = np.fft.fftn(up[a].reshape(nz, ny, nx)) / N
+        e = 0.5 * (uh.real ** 2 + uh.imag ** 2)
+        ok = shell < nshells
+        E += np.bincount(shell[ok], weights=e[ok], minlength=nshells)[:nshells]
+    return E
+
+
 def phi_update(P: OrcParams, phi, u) -> np.ndarray:
     N = ncells(P)
     phi = _f64(phi, (N,))
