@@ -160,6 +160,15 @@ int lbm_nci_diagnostics(lbm_ctx *ctx, double *out);
  * 42 KB of device scratch on the first call; synchronises the context's stream. */
 int lbm_curvature(lbm_ctx *ctx, double kmin, double kmax, int nbins, int64_t *hist, double *out);
 
+/* Carrier-phase kinetic-energy spectrum of the current state (Sec. 3.4): the liquid (phi >= 1/2)
+ * velocity fluctuation u' = chi (u - <u>_liquid), with u the velocity of lbm_read_fields, transformed
+ * per component (cuFFT, real to complex); E[K] = sum over the wave vectors k_a = 2 pi m_a / n_a
+ * with round(|k| / (2 pi / max(n_a))) = K of |u_hat(k)|^2 / 2, u_hat = FFT / N, so that the sum of
+ * all shells is <|u'|^2> / 2. E: nshells doubles (host), 1 <= nshells <= 1024 (else LBM_ERR_ARG);
+ * energy beyond the last shell is not returned. Allocates about 8N bytes of device memory plus the
+ * transform's workspace for the call; LBM_ERR_CUDA if that or the transform fails. Synchronises. */
+int lbm_energy_spectrum(lbm_ctx *ctx, int nshells, double *E);
+
 /* Batches: independent contexts advanced together (a parameter sweep of uneven cases; no
  * counterpart in the paper, which runs one case at a time). One CUDA graph holds two steps of
  * every context, the contexts spread over nstreams concurrent branches, so that small cases fill

@@ -74,6 +74,7 @@ def load():
     L.lbm_mass_noalloc.argtypes = [_VP, _VP, _VP]
     L.lbm_nci_diagnostics.argtypes = [_VP, _VP]
     L.lbm_curvature.argtypes = [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_int, _VP, _VP]
+    L.lbm_energy_spectrum.argtypes = [_VP, ctypes.c_int, _VP]
     L.lbm_batch_create.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.POINTER(_VP)]
     L.lbm_batch_step.argtypes = [_VP, ctypes.c_int]
     L.lbm_batch_synchronize.argtypes = [_VP]
@@ -90,7 +91,7 @@ def load():
     for name in ("lbm_create", "lbm_set_stream", "lbm_init_fields", "lbm_set_state", "lbm_get_state",
                  "lbm_step", "lbm_read_fields", "lbm_mass", "lbm_mass_noalloc", "lbm_read_nci", "lbm_synchronize",
                  "lbm_profile", "lbm_profile_read", "lbm_lattice", "lbm_batch_create", "lbm_batch_step",
-                 "lbm_nci_diagnostics", "lbm_curvature",
+                 "lbm_nci_diagnostics", "lbm_curvature", "lbm_energy_spectrum",
                  "lbm_batch_synchronize"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -243,6 +244,12 @@ def lbm_curvature(ctx: int, kmin: float, kmax: float, nbins: int) -> dict:
     return {"band_cells": float(out[0]), "mean": float(out[1]), "hist": hist}
 
 
+def lbm_energy_spectrum(ctx: int, nshells: int) -> np.ndarray:
+    E = np.zeros(int(nshells))
+    _check(load().lbm_energy_spectrum(_VP(ctx), int(nshells), E.ctypes.data_as(_VP)), "lbm_energy_spectrum")
+    return E
+
+
 def lbm_synchronize(ctx: int) -> None:
     _check(load().lbm_synchronize(_VP(ctx)), "lbm_synchronize")
 
@@ -373,6 +380,9 @@ class Lbm:
 
     def curvature(self, kmin: float, kmax: float, nbins: int):
         return lbm_curvature(self.ctx, kmin, kmax, nbins)
+
+    def energy_spectrum(self, nshells: int):
+        return lbm_energy_spectrum(self.ctx, nshells)
 
     def profile(self, enable=True):
         lbm_profile(self.ctx, enable)

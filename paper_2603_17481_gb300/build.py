@@ -30,6 +30,17 @@ def _nvcc():
     return "nvcc"
 
 
+def _cuda_libdir(nvcc):
+    """The toolkit's library directory (for cuFFT), next to nvcc's bin directory."""
+    import shutil
+    path = os.path.realpath(shutil.which(nvcc) or nvcc)
+    root = os.path.dirname(os.path.dirname(path))
+    for sub in ("lib64", "lib"):
+        if os.path.isdir(os.path.join(root, sub)):
+            return os.path.join(root, sub)
+    return os.path.join(root, "lib64")
+
+
 def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
@@ -68,7 +79,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, "-shared", *ARCH, "-o", tmp, *objs]
+    cmd = [nvcc, "-shared", *ARCH, "-o", tmp, *objs, "-lcufft", "-Xlinker", "-rpath=" + _cuda_libdir(nvcc)]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")

@@ -71,6 +71,13 @@ cudaError_t launch_nci_diag(int dim, const KParams &P, const int32_t *phi, const
 // over the band q >= q_th a histogram of kappa on [kmin, kmax) (nbins <= kMaxCurvBins, integer
 // counts) and the band's cell count and sum of kappa (FP64, fixed order): out = {count, sum}.
 constexpr int kMaxCurvBins = 4096;
+
+// Carrier-phase kinetic-energy spectrum (Sec. 3.4) of the velocity u (3N) into E_dev (nshells
+// doubles on the device), synchronous on s. Returns 0, 1 (bad nshells), 2 (CUDA error or out of
+// memory) or 3 (cuFFT failure). Allocates about 8N bytes plus the transform's workspace per call.
+constexpr int kMaxSpectrumShells = 1024;
+int spectrum_compute(const KParams &P, const int32_t *phi, const float *u, int nshells, double *E_dev,
+                     cudaStream_t s);
 cudaError_t launch_curvature(int dim, const KParams &P, const int32_t *phi, float4 *nrm, float kmin, float kmax,
                              int nbins, unsigned long long *hist, double *partials, double *out, cudaStream_t s);
 

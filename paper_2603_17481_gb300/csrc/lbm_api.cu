@@ -516,6 +516,19 @@ int lbm_curvature(lbm_ctx *c, double kmin, double kmax, int nbins, int64_t *hist
   return LBM_OK;
 }
 
+int lbm_energy_spectrum(lbm_ctx *c, int nshells, double *E) {
+  if (!c || !E || nshells < 1 || nshells > kMaxSpectrumShells) return LBM_ERR_ARG;
+  if (!c->initialised) return LBM_ERR_STATE;
+  int rc = run_moments(c);
+  if (rc) return rc;
+  if ((rc = ensure_stage(c, sizeof(double) * nshells))) return rc;
+  const int r = spectrum_compute(c->K, c->phi[c->pcur], c->mom, nshells, c->stage, c->stream);
+  if (r == 1) return LBM_ERR_ARG;
+  if (r) return LBM_ERR_CUDA;
+  if ((rc = d2h(c, E, c->stage, sizeof(double) * nshells))) return rc;
+  return sync(c);
+}
+
 int lbm_synchronize(lbm_ctx *c) {
   if (!c) return LBM_ERR_ARG;
   return sync(c);
