@@ -548,6 +548,12 @@ def run_swarm(args, world, rank, local):
         ph, _, _ = sim.read_fields(want=("phi",))
         m1, _ = sim.mass()
         kap = sim.curvature(0.0, 0.5, 50)  # kappa = div n, Eq. 78: 2 / R for R in [8, 12] is 0.17-0.25
+        Ek = sim.energy_spectrum(min(L // 2, 1024))
+        kb = L / 20.0  # bubble wavenumber L / d_b
+        ks = np.arange(Ek.size)
+        band = (ks >= kb) & (ks <= 4 * kb) & (Ek > 0)
+        slope = float(np.polyfit(np.log(ks[band]), np.log(Ek[band]), 1)[0]) if band.sum() > 3 else None
+        pick = np.unique(np.geomspace(1, Ek.size - 1, 24).astype(int))
         deq = None
         if np.all(np.isfinite(ph)):
             _, vols = count_bubbles((ph < 0.5).reshape(L, L, L), volumes=True)
@@ -562,6 +568,8 @@ def run_swarm(args, world, rank, local):
                       "kappa": {"mean": round(kap["mean"], 5), "band_cells": kap["band_cells"],
                                 "hist_0_0.5_50": kap["hist"].tolist()},
                       "D_eq": deq,
+                      "E_k": {"shells": pick.tolist(), "E": [float(f"{v:.4g}") for v in Ek[pick]],
+                              "slope_kb_to_4kb": slope, "total": float(Ek.sum())},
                       "phi_mass_drift": abs(m1 - m0) / abs(m0)}
         sim.close()
     if rank != 0:
