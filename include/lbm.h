@@ -163,7 +163,7 @@ int lbm_curvature(lbm_ctx *ctx, double kmin, double kmax, int nbins, int64_t *hi
 /* Carrier-phase kinetic-energy spectrum of the current state (Sec. 3.4): the liquid (phi >= 1/2)
  * velocity fluctuation u' = chi (u - <u>_liquid), with u the velocity of lbm_read_fields, transformed
  * per component (cuFFT, real to complex); E[K] = sum over the wave vectors k_a = 2 pi m_a / n_a
- * with round(|k| / (2 pi / max(n_a))) = K of |u_hat(k)|^2 / 2, u_hat = FFT / N, so that the sum of
+ * with floor(|k| / (2 pi / max(n_a)) + 1/2) = K of |u_hat(k)|^2 / 2, u_hat = FFT / N, so the sum of
  * all shells is <|u'|^2> / 2. E: nshells doubles (host), 1 <= nshells <= 1024 (else LBM_ERR_ARG);
  * energy beyond the last shell is not returned. Allocates about 8N bytes of device memory plus the
  * transform's workspace for the call; LBM_ERR_CUDA if that or the transform fails. Synchronises. */

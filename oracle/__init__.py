@@ -246,7 +246,7 @@ def energy_spectrum(P: OrcParams, phi, u, nshells: int) -> np.ndarray:
     The carrier phase is the liquid, chi = 1 where phi >= 1/2 (reading R23). The fluctuation is
     u' = chi (u - <u>_liquid) and u_hat(k) = (1/N) sum_x u'(x) exp(-i k.x) per component, so that
     sum_k |u_hat|^2 = <|u'|^2> (Parseval). With k_a = 2 pi m_a / n_a and the shell width
-    2 pi / max(n_a), E(K) = sum over k with round(|k| / width) = K of |u_hat(k)|^2 / 2.
+    2 pi / max(n_a), E(K) = sum over k with floor(|k| / width + 1/2) = K of |u_hat(k)|^2 / 2.
     Returns E for K = 0 .. nshells - 1 (energy beyond the last shell is not returned).
     """
     nx, ny, nz = P.nx, P.ny, P.nz
@@ -256,10 +256,13 @@ def energy_spectrum(P: OrcParams, phi, u, nshells: int) -> np.ndarray:
     chi = (phi >= 0.5).astype(np.float64)
     ubar = (u * chi).sum(axis=1) / max(chi.sum(), 1.0)
     up = chi * (u - ubar[:, None])
+    # |k| in units of the shell width: m_a M / n_a with M = max(n_a), exact for the half-integer
+    # ties of boxes such as 96 x 64, which round up
+    M = max(nx, ny, nz)
     m = [np.fft.fftfreq(n, 1.0 / n) for n in (nz, ny, nx)]
-    kk = np.sqrt(sum((2 * np.pi * mm / n)[tuple(slice(None) if i == j else None for j in range(3))] ** 2
+    kk = np.sqrt(sum((mm * M / n)[tuple(slice(None) if i == j else None for j in range(3))] ** 2
                      for i, (mm, n) in enumerate(zip(m, (nz, ny, nx)))))
-    shell = np.rint(kk / (2 * np.pi / max(nx, ny, nz))).astype(np.int64)
+    shell = np.floor(kk + 0.5).astype(np.int64)
     E = np.zeros(nshells)
     for a in range(3):
         uh = np.fft.fftn(up[a].reshape(nz, ny, nx)) / N

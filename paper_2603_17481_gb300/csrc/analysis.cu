@@ -3,7 +3,8 @@
 // The carrier phase is the liquid, chi = 1 where phi >= 1/2. The fluctuation u' = chi (u - <u>_liquid)
 // is transformed per component with a cuFFT real-to-complex 3D transform (the library's FFT; the
 // surrounding kernels are ours), and |u_hat|^2 / 2 with u_hat = FFT / N is summed into shells of
-// |k| (k_a = 2 pi m_a / n_a, shell width 2 pi / max(n_a)); the half spectrum counts twice except
+// |k| (k_a = 2 pi m_a / n_a, shell width 2 pi / max(n_a), shell floor(|k| / width + 1/2), with
+// |k| / width = |(m_a max(n) / n_a)| exact on half-integer ties); the half spectrum counts twice except
 // on the planes m_x = 0 and m_x = n_x / 2.
 #include <cufft.h>
 
@@ -87,7 +88,7 @@ k_shells(const KParams P, const cufftComplex *__restrict__ uh, int nshells, doub
     const int mx = (int)(e % hx), iy = (int)((e / hx) % ny), iz = (int)(e / ((long long)hx * ny));
     const int my = iy < (ny + 1) / 2 ? iy : iy - ny, mz = iz < (nz + 1) / 2 ? iz : iz - nz;
     const double kx = (double)mx * M / nx, ky = (double)my * M / ny, kz = (double)mz * M / nz;
-    const int K = (int)rint(sqrt(kx * kx + ky * ky + kz * kz));
+    const int K = (int)floor(sqrt(kx * kx + ky * ky + kz * kz) + 0.5);  // ties round up
     if (K >= nshells) continue;
     const double w = (mx == 0 || (nx % 2 == 0 && mx == nx / 2)) ? 1.0 : 2.0;
     const cufftComplex v = uh[e];
