@@ -136,6 +136,25 @@ def test_c2_offcentre_3d_200_steps():
     _check_traj(phg, pho, ug, uo)
 
 
+def test_d3q27_collision_200_steps():
+    """The paper's own hydrodynamic lattice, D3Q27, on an off-centre collision (64x40x40, ratio 10,
+    R = 8), 200 steps: max|dphi| <= 1e-5, max|du| <= 1e-6 against the FP64 oracle."""
+    cfg = W.base_config(3, 64, 40, 40, 27, rho_g=0.1)
+    cx, cy, cz = 31.5, 19.5, 19.5
+    phi, u = W.droplet_fields(cfg, [(cx - 12.0, cy - 2.1, cz), (cx + 12.0, cy + 2.1, cz)], [8.0, 8.0],
+                              [(0.02, 0, 0), (-0.02, 0, 0)])
+    phi = W.to_q30_grid(phi)
+    P = O.make_params(cfg)
+    f = O.init(P, phi, u)
+    fo, pho, _ = O.step(P, f, phi, 200)
+    _, uo = O.moments(P, fo, pho)
+    sim = B.Lbm(cfg)
+    sim.init_fields(phi, u)
+    sim.step(200)
+    phg, ug, _ = sim.read_fields()
+    _check_traj(phg, pho, ug, uo)
+
+
 @pytest.mark.parametrize("store,tol", [("f16", 1e-3), ("bf16", 1e-2)])
 def test_half_precision_store_phi_error_and_mass(store, tol):
     """Populations stored as FP16/BF16 (f/w_i) with FP32 arithmetic, ratio-100 collision
