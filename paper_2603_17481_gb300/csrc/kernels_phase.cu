@@ -256,7 +256,7 @@ struct Phase3 {
   static constexpr int NFLG = (ZC / NZ) * FY;
   static constexpr size_t smem = sizeof(float) * (2 * NP + 4 * NQ) + sizeof(int32_t) * 4 * NP +
                                  sizeof(float) * 4 * NP +
-                                 sizeof(float) * (12 * NQ + 2 * NQ + 2 * NC + QX * TY + TX * QY + 2 * NC) +
+                                 sizeof(float) * (NQ + 2 * NQ + 2 * NC + QX * TY + TX * QY + 2 * NC) +
                                  sizeof(int32_t) * (NFX + NFY + 2 * NC + NFLG);
   __device__ static __forceinline__ int pi(int lx, int ly) { return (ly + 2) * PX + lx + 2; }
   __device__ static __forceinline__ int qi(int lx, int ly) { return (ly + 1) * QX + lx + 1; }
@@ -279,8 +279,8 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
   float *PS = RZ + 2 * G::NP;                                // [4][NQ]
   int32_t *PH = reinterpret_cast<int32_t *>(PS + 4 * G::NQ);  // [4][NP] fixed point
   float *PF = reinterpret_cast<float *>(PH + 4 * G::NP);      // [4][NP] FP32 copy
-  float *A = PF + 4 * G::NP;                                 // [4][3][NQ]
-  float *AXZ = A + 12 * G::NQ;                               // [NQ]
+  float *AZ = PF + 4 * G::NP;                                // [NQ]: a_z of plane k + 1
+  float *AXZ = AZ + G::NQ;                                   // [NQ]
   float *AYZ = AXZ + G::NQ;                                  // [NQ]
   float *ASXY = AYZ + G::NQ;                                 // [2][NC]
   float *UX = ASXY + 2 * G::NC;                              // [TY][QX]: lx -1..32 at columns 0..33
@@ -351,6 +351,10 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
     }
   };
   prefetch(zb - 4);
+  // per-thread histories along z: phi of this thread's phi-plane entries (planes k, k + 1) and a_x,
+  // a_y of its halo-1 entries (planes k - 1, k), so the z sums need no shared-memory reads
+  float hpf[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+  float hax[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, hay[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
 
   for (int k = zb - 4; k < ze; k++) {
     const int s4k = (k + 8) & 3, s4k1 = (k + 9) & 3, s4k2 = (k + 10) & 3, s4km = (k + 7) & 3;
@@ -383,10 +387,16 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
     __syncthreads();
     // S2: RZ(k+1) and PSXY(k+2)
     {
-      const float *p0 = PF + s4k * G::NP, *p1 = PF + s4k1 * G::NP, *p2 = PF + s4k2 * G::NP;
-      if (k >= zb - 2) {
-        float *rz = RZ + ((k + 1) & 1) * G::NP;
-        for (int t = tid; t < G::NP; t += G::NT) rz[t] = s141(p0[t], p1[t], p2[t]);
+      const float *p2 = PF + s4k2 * G::NP;
+      float *rz = RZ + ((k + 1) & 1) * G::NP;
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int t = tid + h * G::NT;
+        if (t >= G::NP) break;
+        const float v2 = p2[t];  // phi plane k + 2; planes k and k + 1 of this entry are in registers
+        if (k >= zb - 2) rz[t] = s141(hpf[h][0], hpf[h][1], v2);
+        hpf[h][0] = hpf[h][1];
+        hpf[h][1] = v2;
       }
       float *ps = PS + s4k2 * G::NQ;
 #pragma unroll
@@ -406,7 +416,6 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
       const float *rz = RZ + ((k + 1) & 1) * G::NP;
       const float *psp = PS + s4k2 * G::NQ, *psm = PS + s4k * G::NQ;
       const float *p1 = PF + s4k1 * G::NP;
-      float *a = A + s4k1 * 3 * G::NQ;
       constexpr float gs = 1.0f / 72.0f;
 #pragma unroll
       for (int h = 0; h < 2; h++) {
@@ -422,15 +431,21 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
         const float gg = g0 * g0 + g1 * g1 + g2 * g2;
         const float gn = gg > 0.0f ? gg * rsqrtf(gg) : 0.0f;
         const float sc = __fdividef(ph * (1.0f - ph), gn + P.eps_n);
-        a[t] = g0 * sc;
-        a[G::NQ + t] = g1 * sc;
-        a[2 * G::NQ + t] = g2 * sc;
+        const float ax = g0 * sc, ay = g1 * sc;
+        AZ[t] = g2 * sc;
+        // z-smoothed a_x, a_y of plane k from this entry's planes k - 1, k (registers) and k + 1
+        if (k >= zb) {
+          AXZ[t] = s141(hax[h][0], hax[h][1], ax);
+          AYZ[t] = s141(hay[h][0], hay[h][1], ay);
+        }
+        hax[h][0] = hax[h][1]; hax[h][1] = ax;
+        hay[h][0] = hay[h][1]; hay[h][1] = ay;
       }
     }
     __syncthreads();
-    // S4: z-smoothed compressive components at plane k, in-plane s_x s_y a_z at plane k+1
+    // S4: in-plane s_x s_y a_z at plane k+1 (the z-smoothed a_x, a_y of plane k came with S3)
     if (k >= zb - 2) {
-      const float *az = A + s4k1 * 3 * G::NQ + 2 * G::NQ;
+      const float *az = AZ;
       float *asxy = ASXY + ((k + 1) & 1) * G::NC;
       {
         const int lx = tid & 31, ly = tid >> 5;
@@ -439,16 +454,6 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
         const float r1 = s141(az[c - 1], az[c], az[c + 1]);
         const float r2 = s141(az[c + G::QX - 1], az[c + G::QX], az[c + G::QX + 1]);
         asxy[tid] = s141(r0, r1, r2);
-      }
-      if (k >= zb) {
-        const float *am = A + s4km * 3 * G::NQ, *a0 = A + s4k * 3 * G::NQ, *ap = A + s4k1 * 3 * G::NQ;
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-          const int t = tid + h * G::NT;
-          if (!vq[h]) continue;
-          AXZ[t] = s141(am[t], a0[t], ap[t]);
-          AYZ[t] = s141(am[G::NQ + t], a0[G::NQ + t], ap[G::NQ + t]);
-        }
       }
     }
     __syncthreads();
