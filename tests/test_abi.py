@@ -88,3 +88,29 @@ def test_strerror_and_kernel_names(lib):
 def test_graft_entry_build_runs():
     import __graft_entry__ as g
     g.build()
+
+
+def test_lattice_table_equals_the_oracles(lib, orc):
+    """The library's velocity sets and weights (compile-time tables) against the oracle's, which
+    builds its own from the ordering rule: identical integers and weights."""
+    for dim, Q in ((2, 9), (3, 19), (3, 27)):
+        c, w = lib.lbm_lattice(dim, Q)
+        co, wo = orc.lattice(dim, Q)
+        assert np.array_equal(c, co)
+        assert np.array_equal(w, wo)
+
+
+def test_null_handles_rejected_without_a_gpu(lib):
+    """Every entry point that takes a context or batch handle rejects a null one before any CUDA call."""
+    L = lib.load()
+    out = (ctypes.c_double * 8)()
+    assert L.lbm_step(None, 1) == lib.LBM_ERR_ARG
+    assert L.lbm_mass(None, out, out) == lib.LBM_ERR_ARG
+    assert L.lbm_mass_noalloc(None, out, out) == lib.LBM_ERR_ARG
+    assert L.lbm_read_fields(None, None, None, None) == lib.LBM_ERR_ARG
+    assert L.lbm_nci_diagnostics(None, out) == lib.LBM_ERR_ARG
+    assert L.lbm_curvature(None, 0.0, 1.0, 0, None, out) == lib.LBM_ERR_ARG
+    assert L.lbm_energy_spectrum(None, 4, out) == lib.LBM_ERR_ARG
+    assert L.lbm_batch_step(None, 2) == lib.LBM_ERR_ARG
+    assert L.lbm_batch_create(None, 0, 1, None, None) == lib.LBM_ERR_ARG
+    assert L.lbm_synchronize(None) == lib.LBM_ERR_ARG
