@@ -34,7 +34,8 @@ template <int DIM> struct NciGeom {
   static constexpr int NYR = HX * TY * TZ;  // z- and y-filtered rows
   static constexpr size_t smem = sizeof(int32_t) * NB + sizeof(float) * 3 * NB + sizeof(int) * (NT + 1) +
                                  sizeof(float) * (6 * (NW + 1) + 1) + sizeof(long long) * (HY * HZ + 1) +
-                                 sizeof(int) * HX + sizeof(__half) * 6 * ((DIM == 3 ? NZR : 0) + NYR);
+                                 sizeof(int) * HX + sizeof(__half) * 6 * ((DIM == 3 ? NZR : 0) + NYR) +
+                                 sizeof(float) * NB;
 };
 
 // The eight windows [o, o + 6], o = 0..7, of fourteen values: the suffix extremes of [0, 6] and the
@@ -130,6 +131,8 @@ k_nci_scan(const KParams P, const NciTable T, const int32_t *__restrict__ phi, c
   int *s_col = reinterpret_cast<int *>(s_row + G::HY * G::HZ);                   // [HX]
   __half *s_yr = reinterpret_cast<__half *>(s_col + G::HX);                        // [6][NYR]
   __half *s_zr = s_yr + 6 * G::NYR;                                                // [6][NZR] (3D)
+  // q = phi (1 - phi) of the staged box (phi clamped, binary32 as the gate takes it), computed once
+  float *s_q = reinterpret_cast<float *>(s_zr + 6 * (DIM == 3 ? G::NZR : 0));        // [NB]
 
   const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
   const int tid = tx + G::TX * (ty + G::TY * tz), lane = tid & 31, warp = tid >> 5;
@@ -183,7 +186,11 @@ k_nci_scan(const KParams P, const NciTable T, const int32_t *__restrict__ phi, c
         const int r = warp + h * G::NW;
         if (r < NROWS) {
           s_phi[r * G::HX + lane] = va[h];
-          if (xtra) s_phi[r * G::HX + 32 + lane] = vb[h];
+          s_q[r * G::HX + lane] = q_gate_value(va[h]);
+          if (xtra) {
+            s_phi[r * G::HX + 32 + lane] = vb[h];
+            s_q[r * G::HX + 32 + lane] = q_gate_value(vb[h]);
+          }
         }
       }
       __syncwarp();  // this warp's rows of s_phi and s_row
@@ -193,8 +200,8 @@ k_nci_scan(const KParams P, const NciTable T, const int32_t *__restrict__ phi, c
         const int r = warp + h * G::NW;
         if (r >= NROWS) break;
         const int b = r * G::HX + lane;
-        const bool ga = q_gate_value(s_phi[b]) >= P.q_th;
-        const bool gb = xtra && q_gate_value(s_phi[b + 32]) >= P.q_th;
+        const bool ga = s_q[b] >= P.q_th;
+        const bool gb = xtra && s_q[b + 32] >= P.q_th;
         float4 na, nb;
         if (ga || gb) {
           const long long row = s_row[r];
@@ -244,7 +251,7 @@ k_nci_scan(const KParams P, const NciTable T, const int32_t *__restrict__ phi, c
     const float rhi0 = s_rng[6 * G::NW + 3], rhi1 = s_rng[6 * G::NW + 4], rhi2 = s_rng[6 * G::NW + 5];
     const float thr = P.cos_opp + 1e-5f;
     const int ob0 = (DIM == 3 ? (tz + G::H) * G::HX * G::HY : 0) + (ty + G::H) * G::HX + tx + G::H;
-    if (tiles) gated = inb && q_gate_value(s_phi[ob0]) >= P.q_th;
+    if (tiles) gated = inb && s_q[ob0] >= P.q_th;
     bool scan = false;
     if (gated) {
       const float n0 = s_n[ob0], n1 = s_n[G::NB + ob0], n2 = s_n[2 * G::NB + ob0];
@@ -352,7 +359,7 @@ k_nci_scan(const KParams P, const NciTable T, const int32_t *__restrict__ phi, c
       const int cx = c % G::TX, cy = (c / G::TX) % G::TY, cz = c / (G::TX * G::TY);
       const int ob = (DIM == 3 ? (cz + G::H) * G::HX * G::HY : 0) + (cy + G::H) * G::HX + cx + G::H;
       const int32_t vx = s_phi[ob];
-      const float qxc = q_gate_value(vx);
+      const float qxc = s_q[ob];
       const float n0 = s_n[ob], n1 = s_n[G::NB + ob], n2 = s_n[2 * G::NB + ob];
       unsigned long long best = ~0ull;
       {
@@ -365,7 +372,7 @@ k_nci_scan(const KParams P, const NciTable T, const int32_t *__restrict__ phi, c
           if (j < T.count) {
             const NciOffset o = T.o[j];
             const int yb = ob + o.dx + G::HX * (o.dy + G::HY * o.dz);
-            const float qy = q_gate_value(s_phi[yb]);
+            const float qy = s_q[yb];
             if (qy >= P.q_th && fabsf(__fsub_rn(qy, qxc)) <= sim) {
               const float dot = __fadd_rn(__fadd_rn(__fmul_rn(n0, s_n[yb]), __fmul_rn(n1, s_n[G::NB + yb])),
                                           __fmul_rn(n2, s_n[2 * G::NB + yb]));
@@ -396,7 +403,7 @@ k_nci_scan(const KParams P, const NciTable T, const int32_t *__restrict__ phi, c
         const int yb = ob + o.dx + G::HX * (o.dy + G::HY * o.dz);
         const int32_t vy = s_phi[yb];
         const float m0 = s_n[yb], m1 = s_n[G::NB + yb], m2 = s_n[2 * G::NB + yb];
-        const float qy = q_gate_value(vy);
+        const float qy = s_q[yb];
         // paired indicator and clamp, Eqs. 66-67
         const float qpair = 0.5f * (qxc + qy);
         const float qcl = fminf(fmaxf(qpair, P.eps_q), 0.25f - P.eps_q);
