@@ -30,6 +30,7 @@ struct lbm_ctx {
   int32_t *partner = nullptr;
   int *tiles[2] = {nullptr, nullptr};
   int *ntiles = nullptr;  // 2 counters, one per phi buffer
+  lbm::NciAux aux;        // near-contact prefilter buffers (3D grids with sides multiple of 4)
   int nci_blocks = 0;
   lbm::ReduceOut *red_part = nullptr, *red_out = nullptr;
   lbm::DiagOut *diag_part = nullptr, *diag_out = nullptr;  // film statistics, on first use
@@ -47,4 +48,7 @@ struct lbm_ctx {
   double prof_ms[LBM_K_COUNT] = {0};
   int64_t prof_n[LBM_K_COUNT] = {0};
 };
+
+// The prefilter buffers of the near-contact pass over listed tiles, or nullptr where it does not apply.
+inline const lbm::NciAux *nci_aux(const lbm_ctx *c) { return c->aux.bricks ? &c->aux : nullptr; }
 

@@ -77,41 +77,166 @@ __device__ __forceinline__ void tile_of(int tile, int gtx, int gty, int &bx, int
 }
 
 // Normals of the gated cells of the listed tiles (or of every tile when tiles == nullptr).
+// With the prefilter (3D, listed tiles): every gated cell's force is set to zero here (the scan
+// overwrites it where a partner is found), the tile's flag is set, and the component ranges of
+// the gated normals of each of its sixteen 4x4x4 bricks are stored (empty bricks as [+inf, -inf]).
 template <int DIM>
 __global__ void __launch_bounds__(NciGeom<DIM>::NT)
-k_nci_normals(const KParams P, const int32_t *__restrict__ phi, float4 *__restrict__ nrm,
-              const int *__restrict__ tiles, const int *__restrict__ ntiles, int total, int gtx, int gty) {
+k_nci_normals(const KParams P, const int32_t *__restrict__ phi, float4 *__restrict__ nrm, float4 *__restrict__ frep,
+              const int *__restrict__ tiles, const int *__restrict__ ntiles, int total, int gtx, int gty,
+              const NciAux aux) {
   using G = NciGeom<DIM>;
   using SL = typename StencilOf<DIM>::type;
+  constexpr bool kBricks = DIM == 3;
+  __shared__ float s_part[kBricks ? 16 * 16 * 6 : 1];  // [brick][row of the brick][lo0..hi2]
+  const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+  const int tid = tx + G::TX * (ty + G::TY * tz);
+  const bool bricks = kBricks && aux.bricks != nullptr;  // uniform over the grid
+  if (bricks && blockIdx.x == 0 && tid == 0) *aux.nscan = 0;
   const int n = tiles ? *ntiles : total;
   const int nx = P.nx, ny = P.ny, nz = P.nz;
+  const float inf = __int_as_float(0x7f800000);
   for (int t = blockIdx.x; t < n; t += gridDim.x) {
+    const int tile = tiles ? tiles[t] : t;
     int bx, by, bz;
-    tile_of<DIM>(tiles ? tiles[t] : t, gtx, gty, bx, by, bz);
-    const int x = bx * G::TX + threadIdx.x, y = by * G::TY + threadIdx.y, z = bz * G::TZ + threadIdx.z;
-    if (x >= nx || y >= ny || z >= nz) continue;
-    const int X[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
-    const int Y[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
-    int Z[3] = {0, 0, 0};
-    if (DIM == 3) { Z[0] = z == 0 ? nz - 1 : z - 1; Z[1] = z; Z[2] = z == nz - 1 ? 0 : z + 1; }
-    const long long idx = (long long)x + (long long)nx * (y + (long long)ny * z);
-    const int32_t v = phi[idx];
-    if (!(q_gate_value(v) >= P.q_th)) continue;
+    tile_of<DIM>(tile, gtx, gty, bx, by, bz);
+    const int x = bx * G::TX + tx, y = by * G::TY + ty, z = bz * G::TZ + tz;
+    bool gated = false;
     float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    if (x < nx && y < ny && z < nz) {
+      const long long idx = (long long)x + (long long)nx * (y + (long long)ny * z);
+      gated = q_gate_value(phi[idx]) >= P.q_th;
+      if (gated) {
+        const int X[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
+        const int Y[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
+        int Z[3] = {0, 0, 0};
+        if (DIM == 3) { Z[0] = z == 0 ? nz - 1 : z - 1; Z[1] = z; Z[2] = z == nz - 1 ? 0 : z + 1; }
 #pragma unroll
-    for (int i = 1; i < SL::Q; i++) {
-      if (!positive<SL>(i)) continue;
-      const int c0 = SL::c(i, 0), c1 = SL::c(i, 1), c2 = SL::c(i, 2);
-      const long long ip = (long long)X[1 + c0] + (long long)nx * (Y[1 + c1] + (long long)ny * Z[1 + c2]);
-      const long long im = (long long)X[1 - c0] + (long long)nx * (Y[1 - c1] + (long long)ny * Z[1 - c2]);
-      const float d = SL::w(i) * dphi_of(__ldg(phi + ip), __ldg(phi + im));
-      g0 += c0 * d;
-      g1 += c1 * d;
-      if (DIM == 3) g2 += c2 * d;
+        for (int i = 1; i < SL::Q; i++) {
+          if (!positive<SL>(i)) continue;
+          const int c0 = SL::c(i, 0), c1 = SL::c(i, 1), c2 = SL::c(i, 2);
+          const long long ip = (long long)X[1 + c0] + (long long)nx * (Y[1 + c1] + (long long)ny * Z[1 + c2]);
+          const long long im = (long long)X[1 - c0] + (long long)nx * (Y[1 - c1] + (long long)ny * Z[1 - c2]);
+          const float d = SL::w(i) * dphi_of(__ldg(phi + ip), __ldg(phi + im));
+          g0 += c0 * d;
+          g1 += c1 * d;
+          if (DIM == 3) g2 += c2 * d;
+        }
+        g0 *= 3.0f; g1 *= 3.0f; g2 *= 3.0f;
+        const float inv = 1.0f / (sqrtf(g0 * g0 + g1 * g1 + g2 * g2) + P.eps_n);
+        g0 *= inv; g1 *= inv; g2 *= inv;
+        nrm[idx] = make_float4(g0, g1, g2, 0.0f);
+        if (bricks) frep[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     }
-    g0 *= 3.0f; g1 *= 3.0f; g2 *= 3.0f;
-    const float inv = 1.0f / (sqrtf(g0 * g0 + g1 * g1 + g2 * g2) + P.eps_n);
-    nrm[idx] = make_float4(g0 * inv, g1 * inv, g2 * inv, 0.0f);
+    if constexpr (kBricks) {
+      if (bricks) {
+        static_assert(G::TX == 32 && G::TY == 8 && G::TZ == 4, "sixteen 4x4x4 bricks per tile");
+        if (tid == 0) aux.flags[tile] = 1;
+        // a warp is one x row of the tile: lanes 4k..4k+3 share brick k
+        float v[6] = {gated ? g0 : inf, gated ? g1 : inf, gated ? g2 : inf,
+                      gated ? g0 : -inf, gated ? g1 : -inf, gated ? g2 : -inf};
+#pragma unroll
+        for (int sh = 1; sh <= 2; sh <<= 1) {
+#pragma unroll
+          for (int c = 0; c < 6; c++) {
+            const float o = __shfl_xor_sync(0xffffffffu, v[c], sh);
+            v[c] = c < 3 ? fminf(v[c], o) : fmaxf(v[c], o);
+          }
+        }
+        if ((tx & 3) == 0) {
+          const int b = (tx >> 2) + 8 * (ty >> 2), r = (ty & 3) + 4 * tz;
+#pragma unroll
+          for (int c = 0; c < 6; c++) s_part[(b * 16 + r) * 6 + c] = v[c];
+        }
+        __syncthreads();
+        if (tid < 96) {
+          const int b = tid / 6, c = tid - 6 * (tid / 6);
+          float a = s_part[b * 96 + c];
+#pragma unroll
+          for (int r = 1; r < 16; r++) a = c < 3 ? fminf(a, s_part[(b * 16 + r) * 6 + c]) : fmaxf(a, s_part[(b * 16 + r) * 6 + c]);
+          const int nbx = nx >> 2, nby = ny >> 2;
+          const int gbx = 8 * bx + (b & 7), gby = 2 * by + (b >> 3);
+          if (gbx < nbx && gby < nby) {
+            const long long bi = (long long)gbx + (long long)nbx * (gby + (long long)nby * bz);
+            reinterpret_cast<__half *>(aux.bricks)[8 * bi + c + (c >= 3)] = c < 3 ? __float2half_rd(a) : __float2half_ru(a);
+          }
+        }
+        __syncthreads();  // s_part is reused by the next tile
+      }
+    }
+  }
+}
+
+// One 128-thread block per listed tile (3D). The tile's sixteen bricks are tested against the
+// union of the normal ranges of their 27 neighbouring bricks, a 10x4x3 box of bricks; a brick of a
+// tile that is not listed holds no gated cell and counts as empty. Every window offset of the
+// scan (|r| <= 3) stays inside those 27 bricks, so for a cell x of a brick with ranges [lo, hi]
+// and every gated y in its window, n(x).n(y) >= sum_a min(lo_a L_a, lo_a H_a, hi_a L_a, hi_a H_a),
+// [L, H] being the union (the product is bilinear, so its minimum over the two boxes is at a
+// corner). Where that bound exceeds cos_opp + 1e-5 for all sixteen bricks, no cell of the tile
+// can meet the facing gate (Eq. 62) and the tile keeps the zero force written by the normals
+// pass; otherwise the tile goes to the scan list.
+__global__ void __launch_bounds__(128)
+k_nci_prefilter(const KParams P, const uint4 *__restrict__ bricks, const unsigned char *__restrict__ flags,
+                const int *__restrict__ tiles, const int *__restrict__ ntiles, int *__restrict__ scan_tiles,
+                int *__restrict__ nscan, int gtx, int gty) {
+  constexpr int RX = 10, RY = 4, RZ = 3, NR = RX * RY * RZ;
+  __shared__ float s_r[6][NR];
+  __shared__ float s_b[48];
+  const int tid = threadIdx.x;
+  const int n = *ntiles;
+  const int nbx = P.nx >> 2, nby = P.ny >> 2, nbz = P.nz >> 2;
+  const float inf = __int_as_float(0x7f800000);
+  const float thr = P.cos_opp + 1e-5f;
+  for (int t = blockIdx.x; t < n; t += gridDim.x) {
+    const int tile = tiles[t];
+    int bx, by, bz;
+    tile_of<3>(tile, gtx, gty, bx, by, bz);
+    if (tid < NR) {
+      const int rx = tid % RX, ry = (tid / RX) % RY, rz = tid / (RX * RY);
+      const int gbx = wrapn(8 * bx - 1 + rx, nbx), gby = wrapn(2 * by - 1 + ry, nby), gbz = wrapn(bz - 1 + rz, nbz);
+      float v[6] = {inf, inf, inf, -inf, -inf, -inf};
+      if (flags[(gbx >> 3) + gtx * ((gby >> 1) + gty * gbz)]) {
+        const uint4 w = bricks[(long long)gbx + (long long)nbx * (gby + (long long)nby * gbz)];
+        v[0] = __half2float(__ushort_as_half((unsigned short)(w.x & 0xffffu)));
+        v[1] = __half2float(__ushort_as_half((unsigned short)(w.x >> 16)));
+        v[2] = __half2float(__ushort_as_half((unsigned short)(w.y & 0xffffu)));
+        v[3] = __half2float(__ushort_as_half((unsigned short)(w.z & 0xffffu)));
+        v[4] = __half2float(__ushort_as_half((unsigned short)(w.z >> 16)));
+        v[5] = __half2float(__ushort_as_half((unsigned short)(w.w & 0xffffu)));
+      }
+#pragma unroll
+      for (int c = 0; c < 6; c++) s_r[c][tid] = v[c];
+    }
+    __syncthreads();
+    if (tid < 48) {
+      const int b = tid & 15, a = tid >> 4;
+      const int cx = b & 7, cy = b >> 3;
+      float L = inf, H = -inf;
+#pragma unroll
+      for (int dz = 0; dz < 3; dz++)
+#pragma unroll
+        for (int dy = 0; dy < 3; dy++)
+#pragma unroll
+          for (int dx = 0; dx < 3; dx++) {
+            const int r = (cx + dx) + RX * ((cy + dy) + RY * dz);
+            L = fminf(L, s_r[a][r]);
+            H = fmaxf(H, s_r[3 + a][r]);
+          }
+      const int rc = (cx + 1) + RX * ((cy + 1) + RY);
+      const float lo = s_r[a][rc], hi = s_r[3 + a][rc];
+      s_b[tid] = fminf(fminf(lo * L, lo * H), fminf(hi * L, hi * H));
+    }
+    __syncthreads();
+    bool need = false;
+    if (tid < 16) {
+      const int cx = tid & 7, cy = tid >> 3;
+      const int rc = (cx + 1) + RX * ((cy + 1) + RY);
+      const bool has = 8 * bx + cx < nbx && 2 * by + cy < nby && s_r[0][rc] <= s_r[3][rc];
+      need = has && s_b[tid] + s_b[16 + tid] + s_b[32 + tid] <= thr;
+    }
+    if (__syncthreads_or(need) && tid == 0) scan_tiles[atomicAdd(nscan, 1)] = tile;
   }
 }
 
@@ -119,7 +244,8 @@ template <int DIM>
 __global__ void __launch_bounds__(NciGeom<DIM>::NT, NciGeom<DIM>::NT >= 1024 ? 1 : 2)
 k_nci_scan(const KParams P, const NciTable T, const int32_t *__restrict__ phi, const float4 *__restrict__ nrm,
            float4 *__restrict__ frep, int32_t *__restrict__ partner, int debug, const int *__restrict__ tiles,
-           const int *__restrict__ ntiles, int total, int gtx, int gty) {
+           const int *__restrict__ ntiles, int total, int gtx, int gty, unsigned char *__restrict__ flags,
+           const int *__restrict__ listed, const int *__restrict__ nlisted) {
   using G = NciGeom<DIM>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int32_t *s_phi = reinterpret_cast<int32_t *>(smem_raw);
@@ -138,6 +264,10 @@ k_nci_scan(const KParams P, const NciTable T, const int32_t *__restrict__ phi, c
   const int tid = tx + G::TX * (ty + G::TY * tz), lane = tid & 31, warp = tid >> 5;
   const int nx = P.nx, ny = P.ny, nz = P.nz;
   const int n = tiles ? *ntiles : total;
+  if (flags) {  // the prefilter has read the flags of this step's listed tiles: clear them
+    const int m = *nlisted;
+    for (int i = blockIdx.x * G::NT + tid; i < m; i += gridDim.x * G::NT) flags[listed[i]] = 0;
+  }
 
   for (int t = blockIdx.x; t < n; t += gridDim.x) {
     int bx, by, bz;
@@ -466,7 +596,7 @@ static cudaError_t nci_attr() {
 template <int DIM>
 static cudaError_t launch_nci_dim(const KParams &P, const NciTable &T, const int32_t *phi, float4 *nrm, float4 *frep,
                                   int32_t *partner, int debug, const int *tiles, const int *ntiles, int list_blocks,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, const NciAux *aux) {
   using G = NciGeom<DIM>;
   cudaError_t e = nci_attr<DIM>();
   if (e != cudaSuccess) return e;
@@ -474,17 +604,33 @@ static cudaError_t launch_nci_dim(const KParams &P, const NciTable &T, const int
   const int total = gtx * gty * gtz;
   const int blocks = tiles ? list_blocks : (total < list_blocks * 4 ? total : list_blocks * 4);
   dim3 block(G::TX, G::TY, G::TZ);
-  k_nci_normals<DIM><<<blocks, block, 0, s>>>(P, phi, nrm, tiles, ntiles, total, gtx, gty);
-  k_nci_scan<DIM><<<blocks, block, G::smem, s>>>(P, T, phi, nrm, frep, partner, debug, tiles, ntiles, total, gtx, gty);
+  const bool pre = DIM == 3 && aux && tiles && aux->bricks && nci_aux_applies(DIM, P);
+  const NciAux none{};
+  k_nci_normals<DIM><<<blocks, block, 0, s>>>(P, phi, nrm, frep, tiles, ntiles, total, gtx, gty, pre ? *aux : none);
+  if (!pre) {
+    k_nci_scan<DIM><<<blocks, block, G::smem, s>>>(P, T, phi, nrm, frep, partner, debug, tiles, ntiles, total, gtx,
+                                                   gty, nullptr, nullptr, nullptr);
+    return cudaGetLastError();
+  }
+  k_nci_prefilter<<<16 * list_blocks, 128, 0, s>>>(P, aux->bricks, aux->flags, tiles, ntiles, aux->scan_tiles,
+                                                   aux->nscan, gtx, gty);
+  k_nci_scan<DIM><<<blocks, block, G::smem, s>>>(P, T, phi, nrm, frep, partner, debug, aux->scan_tiles, aux->nscan,
+                                                 total, gtx, gty, aux->flags, tiles, ntiles);
   return cudaGetLastError();
 }
 
 cudaError_t launch_nci(int dim, const KParams &P, const NciTable &T, const int32_t *phi, float4 *nrm, float4 *frep,
                        int32_t *partner, int debug, const int *tiles, const int *ntiles, int list_blocks,
-                       cudaStream_t s) {
-  return dim == 2 ? launch_nci_dim<2>(P, T, phi, nrm, frep, partner, debug, tiles, ntiles, list_blocks, s)
-                  : launch_nci_dim<3>(P, T, phi, nrm, frep, partner, debug, tiles, ntiles, list_blocks, s);
+                       cudaStream_t s, const NciAux *aux) {
+  return dim == 2 ? launch_nci_dim<2>(P, T, phi, nrm, frep, partner, debug, tiles, ntiles, list_blocks, s, aux)
+                  : launch_nci_dim<3>(P, T, phi, nrm, frep, partner, debug, tiles, ntiles, list_blocks, s, aux);
 }
+
+bool nci_aux_applies(int dim, const KParams &P) {
+  return dim == 3 && P.nx % 4 == 0 && P.ny % 4 == 0 && P.nz % 4 == 0;
+}
+
+size_t nci_brick_count(const KParams &P) { return (size_t)(P.nx / 4) * (size_t)(P.ny / 4) * (size_t)(P.nz / 4); }
 
 int nci_list_blocks(int dim) {
   int dev = 0, sms = 0, per = 0;

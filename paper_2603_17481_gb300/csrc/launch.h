@@ -14,12 +14,27 @@ struct NciTable {
 // Kernel modes of the hydrodynamic kernel.
 enum HydroMode { kStep = 0, kMoments = 1 };
 
+// Buffers of the near-contact prefilter (3D grids whose sides are multiples of 4): the component
+// ranges of the gated normals of every 4x4x4 brick, as halves lo0 lo1 lo2 - hi0 hi1 hi2 - (lo
+// rounded down, hi up); a flag per tile, set while the tile is listed for the current phi (zero
+// between steps); the listed tiles that may hold a facing pair, and their count.
+struct NciAux {
+  uint4 *bricks = nullptr;
+  unsigned char *flags = nullptr;
+  int *scan_tiles = nullptr;
+  int *nscan = nullptr;
+};
+bool nci_aux_applies(int dim, const KParams &P);
+size_t nci_brick_count(const KParams &P);
+
 // Normals of the gated cells into nrm, then the window scan writing frep at gated cells.
 // tiles == nullptr: every tile (debug = 1 also writes zero force / no partner at every cell);
-// otherwise only the ntiles listed tiles, walked by list_blocks resident blocks.
+// otherwise only the ntiles listed tiles, walked by list_blocks resident blocks. With aux (listed
+// tiles only), the normals pass also writes zero force at every gated cell and the brick ranges,
+// a prefilter keeps the tiles whose bricks may face another interface, and only those are scanned.
 cudaError_t launch_nci(int dim, const KParams &P, const NciTable &T, const int32_t *phi, float4 *nrm, float4 *frep,
                        int32_t *partner, int debug, const int *tiles, const int *ntiles, int list_blocks,
-                       cudaStream_t s);
+                       cudaStream_t s, const NciAux *aux = nullptr);
 int nci_list_blocks(int dim);
 cudaError_t phase_prepare(int dim);
 

@@ -184,7 +184,7 @@ int run_moments(lbm_ctx *c) {
   if (c->P.nci_on) {
     rc = from_cuda(timed(c, LBM_K_NCI, [&] {
       return launch_nci(d, c->K, c->T, c->phi[c->pcur], c->nrm, c->frep, nullptr, 0, c->tiles[c->pcur],
-                        c->ntiles + c->pcur, c->nci_blocks, c->stream);
+                        c->ntiles + c->pcur, c->nci_blocks, c->stream, nci_aux(c));
     }));
     if (rc) return rc;
   }
@@ -233,6 +233,14 @@ int lbm_create(const lbm_params *p, lbm_ctx **out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->tiles[1], sizeof(int) * ntile);
   if (e == cudaSuccess) e = cudaMalloc(&c->ntiles, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->ntiles, 0, 2 * sizeof(int));
+  if (e == cudaSuccess && p->nci_on && nci_aux_applies(p->dim, c->K)) {
+    e = cudaMalloc(&c->aux.bricks, sizeof(uint4) * nci_brick_count(c->K));
+    if (e == cudaSuccess) e = cudaMalloc(&c->aux.flags, (size_t)ntile);
+    if (e == cudaSuccess) e = cudaMemset(c->aux.flags, 0, (size_t)ntile);
+    if (e == cudaSuccess) e = cudaMalloc(&c->aux.scan_tiles, sizeof(int) * ntile);
+    if (e == cudaSuccess) e = cudaMalloc(&c->aux.nscan, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->aux.nscan, 0, sizeof(int));
+  }
   if (e == cudaSuccess) {
     c->nci_blocks = nci_list_blocks(p->dim);
     if (c->nci_blocks <= 0) e = cudaErrorInvalidConfiguration;
@@ -267,6 +275,7 @@ void lbm_destroy(lbm_ctx *c) {
   cudaFree(c->diag_part); cudaFree(c->diag_out);
   cudaFree(c->curv_hist); cudaFree(c->curv_part);
   cudaFree(c->tiles[0]); cudaFree(c->tiles[1]); cudaFree(c->ntiles);
+  cudaFree(c->aux.bricks); cudaFree(c->aux.flags); cudaFree(c->aux.scan_tiles); cudaFree(c->aux.nscan);
   delete c;
 }
 
@@ -348,7 +357,7 @@ int lbm_step(lbm_ctx *c, int n) {
     if (nci) {
       rc = from_cuda(timed(c, LBM_K_NCI, [&] {
         return launch_nci(d, c->K, c->T, c->phi[c->pcur], c->nrm, c->frep, nullptr, 0, c->tiles[c->pcur],
-                          c->ntiles + c->pcur, c->nci_blocks, c->stream);
+                          c->ntiles + c->pcur, c->nci_blocks, c->stream, nci_aux(c));
       }));
       if (rc) return rc;
     }
@@ -471,7 +480,7 @@ int lbm_nci_diagnostics(lbm_ctx *c, double *out) {
   // the near-contact pass over the tiles listed for the current phi (the list stays for the next step)
   int rc = from_cuda(timed(c, LBM_K_NCI, [&] {
     return launch_nci(c->P.dim, c->K, c->T, c->phi[c->pcur], c->nrm, c->frep, nullptr, 0, c->tiles[c->pcur],
-                      c->ntiles + c->pcur, c->nci_blocks, c->stream);
+                      c->ntiles + c->pcur, c->nci_blocks, c->stream, nci_aux(c));
   }));
   if (rc) return rc;
   rc = from_cuda(timed(c, LBM_K_REDUCE, [&] {

@@ -61,7 +61,7 @@ extern "C" int lbm_mass_noalloc(lbm_ctx *c, double *phi_mass, double *mom) {
   cudaError_t e = cudaSuccess;
   if (c->P.nci_on)
     e = launch_nci(c->P.dim, c->K, c->T, c->phi[c->pcur], c->nrm, c->frep, nullptr, 0, c->tiles[c->pcur],
-                   c->ntiles + c->pcur, c->nci_blocks, c->stream);
+                   c->ntiles + c->pcur, c->nci_blocks, c->stream, nci_aux(c));
   if (e == cudaSuccess)
     e = launch_hydro(c->P.Q, c->P.store, kMoments, c->K, c->pop[c->cur], nullptr, c->phi[c->pcur], c->frep,
                      c->mom, c->mom + 3 * c->N, nullptr, c->stream);

@@ -127,3 +127,38 @@ def _random_state_from(cfg, phi, seed=21):
     P = O.make_params(cfg)
     f = O.init(P, phi, u)
     return P, phi, u, f
+
+
+_CLOSING = {
+    # two pairs closing in (x and z), every side a multiple of 32 x 8 x 4 tiles
+    (64, 48, 40): [((16.3, 20.1, 19.6), 8.0, (0.02, 0.0, 0.0)), ((34.9, 21.2, 20.3), 8.0, (-0.02, 0.0, 0.0)),
+                   ((50.2, 36.4, 12.3), 6.0, (0.0, 0.0, 0.015)), ((50.9, 36.0, 27.6), 7.0, (0.0, 0.0, -0.015))],
+    # partial tiles in x and y (sides multiples of 4 only), one pair across the periodic x boundary
+    (68, 44, 28): [((14.2, 22.3, 13.6), 7.0, (0.02, 0.0, 0.0)), ((31.0, 23.1, 14.2), 8.0, (-0.02, 0.0, 0.0)),
+                   ((63.5, 36.2, 14.1), 6.0, (0.02, 0.0, 0.0)), ((10.0, 36.8, 13.8), 6.0, (-0.02, 0.0, 0.0))],
+}
+
+
+@pytest.mark.parametrize("dims", list(_CLOSING))
+def test_listed_pass_after_steps(dims):
+    """Droplets closing in for 40 steps: the per-step near-contact pass over the listed tiles (with
+    the brick prefilter, which applies where every side is a multiple of 4) then finds exactly the
+    partners and forces of the pass over every tile, and those follow the oracle on the same phi."""
+    cfg = W.base_config(3, *dims, 19, rho_g=0.1)
+    c, R, U = zip(*_CLOSING[dims])
+    phi, u = W.droplet_fields(cfg, c, R, U)
+    sim = B.Lbm(cfg)
+    sim.init_fields(W.to_q30_grid(phi), u)
+    sim.step(40)
+    dl = sim.nci_diagnostics()           # listed tiles, as every step runs it
+    part_all, frep_all = sim.read_nci()  # every tile, no prefilter
+    ph, _, _ = sim.read_fields()
+    sim.close()
+    film = part_all[:, 0] != np.iinfo(np.int32).min
+    assert film.sum() > 20
+    assert dl["V_film"] == film.sum()
+    s = np.sqrt((frep_all[:, film] ** 2).sum(axis=0)).sum()
+    assert abs(dl["sum_rep"] - s) <= 1e-6 * s
+    part_o, _, marg = O.nci(O.make_params(cfg), ph)
+    mis = np.any(part_all != part_o, axis=1)
+    assert np.all(marg[mis] < 1e-5)
