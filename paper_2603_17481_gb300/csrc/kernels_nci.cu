@@ -76,93 +76,157 @@ __device__ __forceinline__ void tile_of(int tile, int gtx, int gty, int &bx, int
   bz = tile / (gtx * gty);
 }
 
-// Normals of the gated cells of the listed tiles (or of every tile when tiles == nullptr).
-// With the prefilter (3D, listed tiles): every gated cell's force is set to zero here (the scan
+// Normals of the gated cells of the listed tiles (or of every tile when tiles == nullptr), 2D.
+__global__ void __launch_bounds__(NciGeom<2>::NT)
+k_nci_normals2(const KParams P, const int32_t *__restrict__ phi, float4 *__restrict__ nrm,
+               const int *__restrict__ tiles, const int *__restrict__ ntiles, int total, int gtx, int gty) {
+  using G = NciGeom<2>;
+  using SL = StencilOf<2>::type;
+  const int n = tiles ? *ntiles : total;
+  const int nx = P.nx, ny = P.ny;
+  for (int t = blockIdx.x; t < n; t += gridDim.x) {
+    int bx, by, bz;
+    tile_of<2>(tiles ? tiles[t] : t, gtx, gty, bx, by, bz);
+    const int x = bx * G::TX + threadIdx.x, y = by * G::TY + threadIdx.y;
+    if (x >= nx || y >= ny) continue;
+    const int X[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
+    const int Y[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
+    const long long idx = (long long)x + (long long)nx * y;
+    if (!(q_gate_value(phi[idx]) >= P.q_th)) continue;
+    float g0 = 0.f, g1 = 0.f;
+#pragma unroll
+    for (int i = 1; i < SL::Q; i++) {
+      if (!positive<SL>(i)) continue;
+      const int c0 = SL::c(i, 0), c1 = SL::c(i, 1);
+      const float d = SL::w(i) * dphi_of(__ldg(phi + X[1 + c0] + (long long)nx * Y[1 + c1]),
+                                         __ldg(phi + X[1 - c0] + (long long)nx * Y[1 - c1]));
+      g0 += c0 * d;
+      g1 += c1 * d;
+    }
+    g0 *= 3.0f; g1 *= 3.0f;
+    const float inv = 1.0f / (sqrtf(g0 * g0 + g1 * g1) + P.eps_n);
+    nrm[idx] = make_float4(g0 * inv, g1 * inv, 0.0f, 0.0f);
+  }
+}
+
+// Normals of the gated cells of the listed tiles (or of every tile when tiles == nullptr), 3D.
+// One 128-thread block per half tile (32 x 4 x 4 cells, eight 4x4x4 bricks side by side in x):
+// phi of the half tile + 1 halo (34 x 6 x 6) is staged in shared memory, then warp w takes the 4
+// rows of plane z0 + w. The gradient is the isotropic D3Q27 one of Eq. 22, summed over the 13
+// links in the same order as everywhere else.
+// With the prefilter (listed tiles): every gated cell's force is set to zero here (the scan
 // overwrites it where a partner is found), the tile's flag is set, and the component ranges of
-// the gated normals of each of its sixteen 4x4x4 bricks are stored (empty bricks as [+inf, -inf]).
-template <int DIM>
-__global__ void __launch_bounds__(NciGeom<DIM>::NT)
-k_nci_normals(const KParams P, const int32_t *__restrict__ phi, float4 *__restrict__ nrm, float4 *__restrict__ frep,
-              const int *__restrict__ tiles, const int *__restrict__ ntiles, int total, int gtx, int gty,
-              const NciAux aux) {
-  using G = NciGeom<DIM>;
-  using SL = typename StencilOf<DIM>::type;
-  constexpr bool kBricks = DIM == 3;
-  __shared__ float s_part[kBricks ? 16 * 16 * 6 : 1];  // [brick][row of the brick][lo0..hi2]
-  const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
-  const int tid = tx + G::TX * (ty + G::TY * tz);
-  const bool bricks = kBricks && aux.bricks != nullptr;  // uniform over the grid
-  if (bricks && blockIdx.x == 0 && tid == 0) *aux.nscan = 0;
+// the gated normals of each brick are stored (empty bricks as [+inf, -inf]).
+constexpr int kNrmThreads = 128;
+struct NrmBox {
+  static constexpr int X = 34, Y = 6, Z = 6, ROWS = Y * Z;  // warp w stages rows w, w + 4, ...
+};
+
+__global__ void __launch_bounds__(kNrmThreads)
+k_nci_normals3(const KParams P, const int32_t *__restrict__ phi, float4 *__restrict__ nrm, float4 *__restrict__ frep,
+               const int *__restrict__ tiles, const int *__restrict__ ntiles, int total, int gtx, int gty,
+               const NciAux aux) {
+  using G = NciGeom<3>;
+  using SL = StencilOf<3>::type;
+  using B = NrmBox;
+  static_assert(G::TX == 32 && G::TY == 8 && G::TZ == 4, "two 32 x 4 x 4 halves per tile");
+  __shared__ int32_t s_box[B::ROWS * B::X];
+  __shared__ float s_part[4][8][6];  // [warp][brick][lo0..hi2]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool bricks = aux.bricks != nullptr;  // uniform over the grid
+  if (bricks && blockIdx.x == 0 && threadIdx.x == 0) *aux.nscan = 0;
   const int n = tiles ? *ntiles : total;
   const int nx = P.nx, ny = P.ny, nz = P.nz;
   const float inf = __int_as_float(0x7f800000);
-  for (int t = blockIdx.x; t < n; t += gridDim.x) {
-    const int tile = tiles ? tiles[t] : t;
+  for (int item = blockIdx.x; item < 2 * n; item += gridDim.x) {
+    const int tile = tiles ? tiles[item >> 1] : (item >> 1);
+    const int half = item & 1;
     int bx, by, bz;
-    tile_of<DIM>(tile, gtx, gty, bx, by, bz);
-    const int x = bx * G::TX + tx, y = by * G::TY + ty, z = bz * G::TZ + tz;
-    bool gated = false;
-    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    if (x < nx && y < ny && z < nz) {
-      const long long idx = (long long)x + (long long)nx * (y + (long long)ny * z);
-      gated = q_gate_value(phi[idx]) >= P.q_th;
-      if (gated) {
-        const int X[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
-        const int Y[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
-        int Z[3] = {0, 0, 0};
-        if (DIM == 3) { Z[0] = z == 0 ? nz - 1 : z - 1; Z[1] = z; Z[2] = z == nz - 1 ? 0 : z + 1; }
+    tile_of<3>(tile, gtx, gty, bx, by, bz);
+    if (bricks && half == 0 && threadIdx.x == 0) aux.flags[tile] = 1;
+    const int x0 = bx * G::TX, y0 = by * G::TY + 4 * half, z0 = bz * G::TZ;
+    {
+      const int xa = wrapn(x0 - 1 + lane, nx), xb = wrapn(x0 + 31 + (lane & 1), nx);
+      int32_t va[9], vb[9];
 #pragma unroll
-        for (int i = 1; i < SL::Q; i++) {
-          if (!positive<SL>(i)) continue;
-          const int c0 = SL::c(i, 0), c1 = SL::c(i, 1), c2 = SL::c(i, 2);
-          const long long ip = (long long)X[1 + c0] + (long long)nx * (Y[1 + c1] + (long long)ny * Z[1 + c2]);
-          const long long im = (long long)X[1 - c0] + (long long)nx * (Y[1 - c1] + (long long)ny * Z[1 - c2]);
-          const float d = SL::w(i) * dphi_of(__ldg(phi + ip), __ldg(phi + im));
-          g0 += c0 * d;
-          g1 += c1 * d;
-          if (DIM == 3) g2 += c2 * d;
-        }
-        g0 *= 3.0f; g1 *= 3.0f; g2 *= 3.0f;
-        const float inv = 1.0f / (sqrtf(g0 * g0 + g1 * g1 + g2 * g2) + P.eps_n);
-        g0 *= inv; g1 *= inv; g2 *= inv;
-        nrm[idx] = make_float4(g0, g1, g2, 0.0f);
-        if (bricks) frep[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int j = 0; j < 9; j++) {
+        const int r = warp + 4 * j, ry = r % B::Y, rz = r / B::Y;
+        const long long row = (long long)nx * (wrapn(y0 - 1 + ry, ny) + (long long)ny * wrapn(z0 - 1 + rz, nz));
+        va[j] = phi[row + xa];
+        if (lane < 2) vb[j] = phi[row + xb];
+      }
+#pragma unroll
+      for (int j = 0; j < 9; j++) {
+        const int r = warp + 4 * j;
+        s_box[r * B::X + lane] = va[j];
+        if (lane < 2) s_box[r * B::X + 32 + lane] = vb[j];
       }
     }
-    if constexpr (kBricks) {
+    __syncthreads();
+    const int x = x0 + lane, z = z0 + warp;
+    const bool xin = x < nx && z < nz;
+    float lo0 = inf, lo1 = inf, lo2 = inf, hi0 = -inf, hi1 = -inf, hi2 = -inf;
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      const int y = y0 + r;
+      const int o = ((warp + 1) * B::Y + r + 1) * B::X + lane + 1;
+      if (!(xin && y < ny && q_gate_value(s_box[o]) >= P.q_th)) continue;
+      float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+#pragma unroll
+      for (int i = 1; i < SL::Q; i++) {
+        if (!positive<SL>(i)) continue;
+        const int c0 = SL::c(i, 0), c1 = SL::c(i, 1), c2 = SL::c(i, 2);
+        const int off = c0 + B::X * (c1 + B::Y * c2);
+        const float d = SL::w(i) * dphi_of(s_box[o + off], s_box[o - off]);
+        g0 += c0 * d;
+        g1 += c1 * d;
+        g2 += c2 * d;
+      }
+      g0 *= 3.0f; g1 *= 3.0f; g2 *= 3.0f;
+      const float inv = 1.0f / (sqrtf(g0 * g0 + g1 * g1 + g2 * g2) + P.eps_n);
+      g0 *= inv; g1 *= inv; g2 *= inv;
+      const long long idx = (long long)x + (long long)nx * (y + (long long)ny * z);
+      nrm[idx] = make_float4(g0, g1, g2, 0.0f);
       if (bricks) {
-        static_assert(G::TX == 32 && G::TY == 8 && G::TZ == 4, "sixteen 4x4x4 bricks per tile");
-        if (tid == 0) aux.flags[tile] = 1;
-        // a warp is one x row of the tile: lanes 4k..4k+3 share brick k
-        float v[6] = {gated ? g0 : inf, gated ? g1 : inf, gated ? g2 : inf,
-                      gated ? g0 : -inf, gated ? g1 : -inf, gated ? g2 : -inf};
+        frep[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+        lo0 = fminf(lo0, g0); lo1 = fminf(lo1, g1); lo2 = fminf(lo2, g2);
+        hi0 = fmaxf(hi0, g0); hi1 = fmaxf(hi1, g1); hi2 = fmaxf(hi2, g2);
+      }
+    }
+    if (bricks) {  // lanes 4k..4k+3 of each warp share brick k; the four planes meet in shared memory
 #pragma unroll
-        for (int sh = 1; sh <= 2; sh <<= 1) {
+      for (int sh = 1; sh <= 2; sh <<= 1) {
+        lo0 = fminf(lo0, __shfl_xor_sync(0xffffffffu, lo0, sh));
+        lo1 = fminf(lo1, __shfl_xor_sync(0xffffffffu, lo1, sh));
+        lo2 = fminf(lo2, __shfl_xor_sync(0xffffffffu, lo2, sh));
+        hi0 = fmaxf(hi0, __shfl_xor_sync(0xffffffffu, hi0, sh));
+        hi1 = fmaxf(hi1, __shfl_xor_sync(0xffffffffu, hi1, sh));
+        hi2 = fmaxf(hi2, __shfl_xor_sync(0xffffffffu, hi2, sh));
+      }
+      if ((lane & 3) == 0) {
+        float *sp = s_part[warp][lane >> 2];
+        sp[0] = lo0; sp[1] = lo1; sp[2] = lo2; sp[3] = hi0; sp[4] = hi1; sp[5] = hi2;
+      }
+    }
+    __syncthreads();  // s_part complete; s_box and s_part are free for the next item after this
+    if (bricks) {
+      const int k = threadIdx.x;
+      const int gbx = 8 * bx + k, gby = 2 * by + half;
+      if (k < 8 && gbx < (nx >> 2) && gby < (ny >> 2)) {
+        float v[6];
 #pragma unroll
-          for (int c = 0; c < 6; c++) {
-            const float o = __shfl_xor_sync(0xffffffffu, v[c], sh);
-            v[c] = c < 3 ? fminf(v[c], o) : fmaxf(v[c], o);
-          }
+        for (int c = 0; c < 6; c++) {
+          v[c] = s_part[0][k][c];
+#pragma unroll
+          for (int w = 1; w < 4; w++) v[c] = c < 3 ? fminf(v[c], s_part[w][k][c]) : fmaxf(v[c], s_part[w][k][c]);
         }
-        if ((tx & 3) == 0) {
-          const int b = (tx >> 2) + 8 * (ty >> 2), r = (ty & 3) + 4 * tz;
-#pragma unroll
-          for (int c = 0; c < 6; c++) s_part[(b * 16 + r) * 6 + c] = v[c];
-        }
-        __syncthreads();
-        if (tid < 96) {
-          const int b = tid / 6, c = tid - 6 * (tid / 6);
-          float a = s_part[b * 96 + c];
-#pragma unroll
-          for (int r = 1; r < 16; r++) a = c < 3 ? fminf(a, s_part[(b * 16 + r) * 6 + c]) : fmaxf(a, s_part[(b * 16 + r) * 6 + c]);
-          const int nbx = nx >> 2, nby = ny >> 2;
-          const int gbx = 8 * bx + (b & 7), gby = 2 * by + (b >> 3);
-          if (gbx < nbx && gby < nby) {
-            const long long bi = (long long)gbx + (long long)nbx * (gby + (long long)nby * bz);
-            reinterpret_cast<__half *>(aux.bricks)[8 * bi + c + (c >= 3)] = c < 3 ? __float2half_rd(a) : __float2half_ru(a);
-          }
-        }
-        __syncthreads();  // s_part is reused by the next tile
+        const auto h = [](__half q) { return (unsigned)__half_as_ushort(q); };
+        uint4 o;
+        o.x = h(__float2half_rd(v[0])) | (h(__float2half_rd(v[1])) << 16);
+        o.y = h(__float2half_rd(v[2]));
+        o.z = h(__float2half_ru(v[3])) | (h(__float2half_ru(v[4])) << 16);
+        o.w = h(__float2half_ru(v[5]));
+        aux.bricks[(long long)gbx + (long long)(nx >> 2) * (gby + (long long)(ny >> 2) * bz)] = o;
       }
     }
   }
@@ -606,7 +670,13 @@ static cudaError_t launch_nci_dim(const KParams &P, const NciTable &T, const int
   dim3 block(G::TX, G::TY, G::TZ);
   const bool pre = DIM == 3 && aux && tiles && aux->bricks && nci_aux_applies(DIM, P);
   const NciAux none{};
-  k_nci_normals<DIM><<<blocks, block, 0, s>>>(P, phi, nrm, frep, tiles, ntiles, total, gtx, gty, pre ? *aux : none);
+  if constexpr (DIM == 2) {
+    k_nci_normals2<<<blocks, block, 0, s>>>(P, phi, nrm, tiles, ntiles, total, gtx, gty);
+  } else {
+    // one block per half tile, at most 16 blocks per resident scan block (grid-stride beyond)
+    const int nb = 2 * total < 16 * list_blocks ? 2 * total : 16 * list_blocks;
+    k_nci_normals3<<<nb, kNrmThreads, 0, s>>>(P, phi, nrm, frep, tiles, ntiles, total, gtx, gty, pre ? *aux : none);
+  }
   if (!pre) {
     k_nci_scan<DIM><<<blocks, block, G::smem, s>>>(P, T, phi, nrm, frep, partner, debug, tiles, ntiles, total, gtx,
                                                    gty, nullptr, nullptr, nullptr);
