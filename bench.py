@@ -32,6 +32,15 @@ WORKLOAD = "3D head-on droplet collision 256x128x128 D3Q{Q}, R=24, W=4, density 
 HBM_FALLBACK_GBS = 6800.0
 # Algorithmic bytes per cell update (stored state only): populations read + written, phi read +
 # written, velocity written + read.
+def kernels_per_step(cfg):
+    """Kernels one lbm_step launches: hydro and phase, plus the near-contact normals and scan and,
+    on 3D grids whose sides are multiples of 4, the brick prefilter between them."""
+    if not cfg["nci_on"]:
+        return 2
+    prefilter = cfg["dim"] == 3 and all(cfg[k] % 4 == 0 for k in ("nx", "ny", "nz"))
+    return 5 if prefilter else 4
+
+
 def step_bytes_per_cell(Q, pop_bytes):
     return 2 * Q * pop_bytes + 8 + 24
 
@@ -389,7 +398,7 @@ def run_sweep(args, world, rank, local):
         m0.append(s.mass()[0])
         sims.append(s)
     cells = sum(s.N for s in sims)
-    kernels_per_step = sum(4 if c["nci_on"] else 2 for c in cfgs)
+    launches_per_step = sum(kernels_per_step(c) for c in cfgs)
     steps = args.steps + (args.steps & 1)  # whole graph launches
 
     def timed(run, k):
@@ -454,7 +463,7 @@ def run_sweep(args, world, rank, local):
         "by_graph_branches": {str(ns): round(v[0], 1) for ns, v in results.items()},
         "step_roofline": {"bytes_per_cell": step_bytes_per_cell(19, 4), "frac_of_measured": round(frac, 4),
                           "peak": peak, "peak_source": peak_kind},
-        "gpu_launches": kernels_per_step * steps,
+        "gpu_launches": launches_per_step * steps,
         "clocks": clocks,
         "phi_mass_drift_max": drift, "nonfinite_cases": nonfinite,
     }
@@ -589,7 +598,7 @@ def run_swarm(args, world, rank, local):
                           "peak": peak, "peak_source": peak_kind},
         "nci_overhead": round(runs["nci_off"]["value"] / on - 1.0, 4),
         "bubbles_initial": nb0, "runs": runs,
-        "gpu_launches": int(4 * args.steps),
+        "gpu_launches": int(kernels_per_step(dict(cfg, nci_on=1)) * args.steps),
     }
 
 

@@ -195,8 +195,10 @@ int lbm_synchronize(lbm_ctx *ctx);
 
 /* Per-kernel timing with CUDA events on the context stream (enable = 1 starts a fresh tally). */
 int lbm_profile(lbm_ctx *ctx, int enable);
-/* Accumulated device milliseconds and launch counts per lbm_kernel_kind (arrays of LBM_K_COUNT;
- * either may be NULL). Synchronises the stream. */
+/* Accumulated device milliseconds and kernel launch counts per lbm_kernel_kind (arrays of
+ * LBM_K_COUNT; either may be NULL). A pass of several kernels counts each of them: the near-contact
+ * pass over the listed tiles is 3 kernels where the brick prefilter applies (3D, every side a
+ * multiple of 4) and 2 elsewhere; a reduction is 2. Synchronises the stream. */
 int lbm_profile_read(lbm_ctx *ctx, double *ms, int64_t *launches);
 
 /* Velocity table of a hydrodynamic lattice in the order above: c is 3*Q ints, w is Q doubles. */

@@ -8,6 +8,7 @@
 
 struct ProfPair {
   int kind;
+  int kernels;  // kernel launches between the two events
   cudaEvent_t a, b;
 };
 
@@ -51,4 +52,6 @@ struct lbm_ctx {
 
 // The prefilter buffers of the near-contact pass over listed tiles, or nullptr where it does not apply.
 inline const lbm::NciAux *nci_aux(const lbm_ctx *c) { return c->aux.bricks ? &c->aux : nullptr; }
+// Kernels of one near-contact pass over the listed tiles: normals, prefilter (where it applies), scan.
+inline int nci_list_kernels(const lbm_ctx *c) { return nci_aux(c) ? 3 : 2; }
 

@@ -43,14 +43,14 @@ cudaEvent_t take_event(lbm_ctx *c) {
 }
 
 // Wraps one launch in a pair of events when the profiler is on.
-template <class F> cudaError_t timed(lbm_ctx *c, int kind, F &&launch) {
+template <class F> cudaError_t timed(lbm_ctx *c, int kind, F &&launch, int kernels = 1) {
   if (!c->prof) return launch();
   cudaEvent_t a = take_event(c), b = take_event(c);
   if (!a || !b) return cudaErrorMemoryAllocation;
   cudaEventRecord(a, c->stream);
   cudaError_t e = launch();
   cudaEventRecord(b, c->stream);
-  c->pairs.push_back({kind, a, b});
+  c->pairs.push_back({kind, kernels, a, b});
   return e;
 }
 
@@ -185,7 +185,7 @@ int run_moments(lbm_ctx *c) {
     rc = from_cuda(timed(c, LBM_K_NCI, [&] {
       return launch_nci(d, c->K, c->T, c->phi[c->pcur], c->nrm, c->frep, nullptr, 0, c->tiles[c->pcur],
                         c->ntiles + c->pcur, c->nci_blocks, c->stream, nci_aux(c));
-    }));
+    }, nci_list_kernels(c)));
     if (rc) return rc;
   }
   return from_cuda(timed(c, LBM_K_HYDRO, [&] {
@@ -358,7 +358,7 @@ int lbm_step(lbm_ctx *c, int n) {
       rc = from_cuda(timed(c, LBM_K_NCI, [&] {
         return launch_nci(d, c->K, c->T, c->phi[c->pcur], c->nrm, c->frep, nullptr, 0, c->tiles[c->pcur],
                           c->ntiles + c->pcur, c->nci_blocks, c->stream, nci_aux(c));
-      }));
+      }, nci_list_kernels(c)));
       if (rc) return rc;
     }
     rc = from_cuda(timed(c, LBM_K_HYDRO, [&] {
@@ -377,7 +377,7 @@ int lbm_step(lbm_ctx *c, int n) {
     if (c->P.mass_check_every > 0 && c->steps % c->P.mass_check_every == 0) {
       rc = from_cuda(timed(c, LBM_K_REDUCE, [&] {
         return launch_reduce(c->K, c->phi[c->pcur], c->u, c->red_part, c->red_out, c->stream);
-      }));
+      }, 2));
       if (rc) return rc;
       ReduceOut r;
       if ((rc = d2h(c, &r, c->red_out, sizeof(r)))) return rc;
@@ -424,7 +424,7 @@ int lbm_mass(lbm_ctx *c, double *phi_mass, double *mom) {
   if (rc) return rc;
   rc = from_cuda(timed(c, LBM_K_REDUCE, [&] {
     return launch_reduce(c->K, c->phi[c->pcur], c->mom, c->red_part, c->red_out, c->stream);
-  }));
+  }, 2));
   if (rc) return rc;
   ReduceOut r;
   if ((rc = d2h(c, &r, c->red_out, sizeof(r)))) return rc;
@@ -451,7 +451,7 @@ int lbm_read_nci(lbm_ctx *c, int32_t *partner, double *frep) {
   rc = from_cuda(timed(c, LBM_K_NCI, [&] {
     return launch_nci(c->P.dim, c->K, c->T, c->phi[c->pcur], c->nrm, c->frep, c->partner, 1, nullptr, nullptr,
                       c->nci_blocks, c->stream);
-  }));
+  }, 2));
   if (rc) return rc;
   if (partner && (rc = d2h(c, partner, c->partner, sizeof(int32_t) * 3 * N))) return rc;
   if (frep) {
@@ -481,11 +481,11 @@ int lbm_nci_diagnostics(lbm_ctx *c, double *out) {
   int rc = from_cuda(timed(c, LBM_K_NCI, [&] {
     return launch_nci(c->P.dim, c->K, c->T, c->phi[c->pcur], c->nrm, c->frep, nullptr, 0, c->tiles[c->pcur],
                       c->ntiles + c->pcur, c->nci_blocks, c->stream, nci_aux(c));
-  }));
+  }, nci_list_kernels(c)));
   if (rc) return rc;
   rc = from_cuda(timed(c, LBM_K_REDUCE, [&] {
     return launch_nci_diag(c->P.dim, c->K, c->phi[c->pcur], c->frep, c->diag_part, c->diag_out, c->stream);
-  }));
+  }, 2));
   if (rc) return rc;
   DiagOut d;
   if ((rc = d2h(c, &d, c->diag_out, sizeof(d)))) return rc;
@@ -514,7 +514,7 @@ int lbm_curvature(lbm_ctx *c, double kmin, double kmax, int nbins, int64_t *hist
   int rc = from_cuda(timed(c, LBM_K_REDUCE, [&] {
     return launch_curvature(c->P.dim, c->K, c->phi[c->pcur], c->nrm, (float)kmin, (float)kmax, nbins > 0 ? nbins : 1,
                             c->curv_hist, c->curv_part, res, c->stream);
-  }));
+  }, 3));
   if (rc) return rc;
   double r[2];
   if ((rc = d2h(c, r, res, sizeof(r)))) return rc;
@@ -567,7 +567,7 @@ int lbm_profile_read(lbm_ctx *c, double *ms, int64_t *launches) {
   for (auto &pp : c->pairs) {
     float t = 0.f;
     if (cudaEventElapsedTime(&t, pp.a, pp.b) == cudaSuccess) c->prof_ms[pp.kind] += t;
-    c->prof_n[pp.kind] += 1;
+    c->prof_n[pp.kind] += pp.kernels;
     c->pool.push_back(pp.a);
     c->pool.push_back(pp.b);
   }

@@ -87,3 +87,13 @@ def test_workload_extras_do_not_shadow_parameters():
         assert cfg["D"] == base["D"] and cfg["p"] == base["p"] and cfg["eps"] == base["eps"]
         extra = set(cfg) - set(base)
         assert not extra & set(O._FIELDS)
+
+
+def test_kernels_per_step():
+    """Kernel launches of one step as the bench claims them: the brick prefilter adds one kernel on 3D
+    grids whose sides are multiples of 4."""
+    assert bench.kernels_per_step(W.base_config(3, 64, 48, 40, 19)) == 5
+    assert bench.kernels_per_step(W.base_config(3, 37, 21, 13, 19)) == 4
+    assert bench.kernels_per_step(W.base_config(3, 64, 48, 40, 19, nci_on=0)) == 2
+    assert bench.kernels_per_step(W.base_config(2, 128, 64, 1, 9)) == 4
+    assert all(bench.kernels_per_step(c) == 5 for c in W.c4_sweep(8))
