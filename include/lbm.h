@@ -193,8 +193,13 @@ void lbm_batch_destroy(lbm_batch *b);
 /* Waits for all work of ctx. */
 int lbm_synchronize(lbm_ctx *ctx);
 
-/* Per-kernel timing with CUDA events on the context stream (enable = 1 starts a fresh tally). */
+/* Per-kernel timing with CUDA events on the context stream (enable = 1 starts a fresh tally of every
+ * kind, enable = 0 stops). Each timed pass records two events on the stream, which adds a little
+ * time between kernels. */
 int lbm_profile(lbm_ctx *ctx, int enable);
+/* As lbm_profile, timing only the kinds whose bit (1u << kind) is set in mask; mask = 0 stops. Bits
+ * of kinds beyond LBM_K_COUNT are ignored. */
+int lbm_profile_kinds(lbm_ctx *ctx, unsigned mask);
 /* Accumulated device milliseconds and kernel launch counts per lbm_kernel_kind (arrays of
  * LBM_K_COUNT; either may be NULL). A pass of several kernels counts each of them: the near-contact
  * pass over the listed tiles is 3 kernels where the brick prefilter applies (3D, every side a

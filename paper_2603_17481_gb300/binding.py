@@ -82,6 +82,7 @@ def load():
     L.lbm_batch_destroy.restype = None
     L.lbm_synchronize.argtypes = [_VP]
     L.lbm_profile.argtypes = [_VP, ctypes.c_int]
+    L.lbm_profile_kinds.argtypes = [_VP, ctypes.c_uint]
     L.lbm_profile_read.argtypes = [_VP, _VP, _VP]
     L.lbm_lattice.argtypes = [ctypes.c_int, ctypes.c_int, _VP, _VP]
     L.lbm_strerror.argtypes = [ctypes.c_int]
@@ -90,7 +91,7 @@ def load():
     L.lbm_kernel_name.restype = ctypes.c_char_p
     for name in ("lbm_create", "lbm_set_stream", "lbm_init_fields", "lbm_set_state", "lbm_get_state",
                  "lbm_step", "lbm_read_fields", "lbm_mass", "lbm_mass_noalloc", "lbm_read_nci", "lbm_synchronize",
-                 "lbm_profile", "lbm_profile_read", "lbm_lattice", "lbm_batch_create", "lbm_batch_step",
+                 "lbm_profile", "lbm_profile_kinds", "lbm_profile_read", "lbm_lattice", "lbm_batch_create", "lbm_batch_step",
                  "lbm_nci_diagnostics", "lbm_curvature", "lbm_energy_spectrum",
                  "lbm_batch_synchronize"):
         getattr(L, name).restype = ctypes.c_int
@@ -258,6 +259,14 @@ def lbm_profile(ctx: int, enable: bool) -> None:
     _check(load().lbm_profile(_VP(ctx), int(bool(enable))), "lbm_profile")
 
 
+def lbm_profile_kinds(ctx: int, kinds) -> None:
+    """Times only the named kernel kinds (names of KERNEL_KINDS); an empty list stops the profiler."""
+    mask = 0
+    for k in kinds:
+        mask |= 1 << KERNEL_KINDS.index(k)
+    _check(load().lbm_profile_kinds(_VP(ctx), mask), "lbm_profile_kinds")
+
+
 def lbm_profile_read(ctx: int):
     ms = np.zeros(len(KERNEL_KINDS))
     n = np.zeros(len(KERNEL_KINDS), dtype=np.int64)
@@ -386,6 +395,9 @@ class Lbm:
 
     def profile(self, enable=True):
         lbm_profile(self.ctx, enable)
+
+    def profile_kinds(self, kinds):
+        lbm_profile_kinds(self.ctx, kinds)
 
     def profile_read(self):
         return lbm_profile_read(self.ctx)

@@ -44,6 +44,7 @@ struct lbm_ctx {
   long long phi_q30_ref = 0;
   // profiler
   bool prof = false;
+  unsigned prof_mask = 0;  // kinds timed while prof is on
   std::vector<ProfPair> pairs;
   std::vector<cudaEvent_t> pool;
   double prof_ms[LBM_K_COUNT] = {0};

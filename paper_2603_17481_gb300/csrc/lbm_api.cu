@@ -44,7 +44,7 @@ cudaEvent_t take_event(lbm_ctx *c) {
 
 // Wraps one launch in a pair of events when the profiler is on.
 template <class F> cudaError_t timed(lbm_ctx *c, int kind, F &&launch, int kernels = 1) {
-  if (!c->prof) return launch();
+  if (!c->prof || !((c->prof_mask >> kind) & 1u)) return launch();
   cudaEvent_t a = take_event(c), b = take_event(c);
   if (!a || !b) return cudaErrorMemoryAllocation;
   cudaEventRecord(a, c->stream);
@@ -543,7 +543,9 @@ int lbm_synchronize(lbm_ctx *c) {
   return sync(c);
 }
 
-int lbm_profile(lbm_ctx *c, int enable) {
+int lbm_profile(lbm_ctx *c, int enable) { return lbm_profile_kinds(c, enable ? ~0u : 0u); }
+
+int lbm_profile_kinds(lbm_ctx *c, unsigned mask) {
   if (!c) return LBM_ERR_ARG;
   int rc = sync(c);
   if (rc) return rc;
@@ -556,7 +558,8 @@ int lbm_profile(lbm_ctx *c, int enable) {
     c->prof_ms[k] = 0;
     c->prof_n[k] = 0;
   }
-  c->prof = enable != 0;
+  c->prof_mask = mask & ((1u << LBM_K_COUNT) - 1u);
+  c->prof = c->prof_mask != 0;
   return LBM_OK;
 }
 

@@ -114,3 +114,5 @@ def test_null_handles_rejected_without_a_gpu(lib):
     assert L.lbm_batch_step(None, 2) == lib.LBM_ERR_ARG
     assert L.lbm_batch_create(None, 0, 1, None, None) == lib.LBM_ERR_ARG
     assert L.lbm_synchronize(None) == lib.LBM_ERR_ARG
+    assert L.lbm_profile(None, 1) == lib.LBM_ERR_ARG
+    assert L.lbm_profile_kinds(None, 2) == lib.LBM_ERR_ARG
