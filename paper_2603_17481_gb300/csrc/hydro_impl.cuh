@@ -26,6 +26,8 @@
 // so each pair of opposite directions shares its even and odd parts.
 #pragma once
 
+#include <type_traits>
+
 #include "launch.h"
 
 // Resident blocks per SM (256 threads each) that the register allocation is sized for: 5 (48
@@ -36,7 +38,10 @@
 
 namespace lbm {
 
-template <class L, int S, int MODE>
+// I32: every population and velocity element offset fits in an unsigned 32-bit integer (Q N <= 2^32,
+// checked by the launcher), so a pull or store address is one 32-bit multiply-add and one widening
+// add; otherwise the offsets are 64-bit.
+template <class L, int S, int MODE, bool I32>
 __global__ void __launch_bounds__(Tile<L::D>::X * Tile<L::D>::Y * Tile<L::D>::Z, L::Q >= 27 ? 4 : LBM_HYDRO_MINB)
 k_hydro(const KParams P, const typename Store<S>::T *__restrict__ src, typename Store<S>::T *__restrict__ dst,
         const int32_t *__restrict__ phi, const float4 *__restrict__ frep, float *__restrict__ u_out,
@@ -87,13 +92,15 @@ k_hydro(const KParams P, const typename Store<S>::T *__restrict__ src, typename 
       for (int b = 0; b < 3; b++) RB[a][b] = nx * (Y[a] + ny * Z[b]);
   }
   const int idx = x + RB[1][1];
+  using Off = typename std::conditional<I32, unsigned, long long>::type;
+  const Off NO = (Off)N;
 
   // pull: f_i(x) = src_i(x - c_i)
   float f[L::Q];
 #pragma unroll
   for (int i = 0; i < L::Q; i++) {
     const int s = X[1 - L::c(i, 0)] + RB[1 - L::c(i, 1)][1 - L::c(i, 2)];
-    f[i] = Store<S>::ld(src + (long long)i * N + s, L::w(i));
+    f[i] = Store<S>::ld(src + ((Off)i * NO + (Off)s), L::w(i));
   }
 
   // isotropic gradient and Laplacian of phi (Eqs. 22-23)
@@ -172,8 +179,8 @@ k_hydro(const KParams P, const typename Store<S>::T *__restrict__ src, typename 
 
   if (MODE == kMoments) {
     u_out[idx] = u0;
-    u_out[N + idx] = u1;
-    u_out[2 * N + idx] = u2;
+    u_out[NO + (Off)idx] = u1;
+    u_out[2 * NO + (Off)idx] = u2;
     ps_out[idx] = ps;
     return;
   }
@@ -242,10 +249,10 @@ k_hydro(const KParams P, const typename Store<S>::T *__restrict__ src, typename 
           pp++;
         }
       }
-      Store<S>::st_w(dst + (long long)ia * N + idx, fpos.x, L::w(ia));
-      Store<S>::st_w(dst + (long long)L::opp(ia) * N + idx, fneg.x, L::w(ia));
-      Store<S>::st_w(dst + (long long)ib * N + idx, fpos.y, L::w(ib));
-      Store<S>::st_w(dst + (long long)L::opp(ib) * N + idx, fneg.y, L::w(ib));
+      Store<S>::st_w(dst + ((Off)ia * NO + (Off)idx), fpos.x, L::w(ia));
+      Store<S>::st_w(dst + ((Off)L::opp(ia) * NO + (Off)idx), fneg.x, L::w(ia));
+      Store<S>::st_w(dst + ((Off)ib * NO + (Off)idx), fpos.y, L::w(ib));
+      Store<S>::st_w(dst + ((Off)L::opp(ib) * NO + (Off)idx), fneg.y, L::w(ib));
     } else {
       const float cu = pcu[p], cr = pcr[p], cAc = pcac[p], cAu = pcau[p];
       const float ev = C0 + cu * (4.5f * cu + 4.5f * cr) + k45 * cAc;
@@ -260,13 +267,13 @@ k_hydro(const KParams P, const typename Store<S>::T *__restrict__ src, typename 
           pp++;
         }
       }
-      Store<S>::st_w(dst + (long long)ia * N + idx, ev + od, L::w(ia));
-      Store<S>::st_w(dst + (long long)L::opp(ia) * N + idx, ev - od, L::w(ia));
+      Store<S>::st_w(dst + ((Off)ia * NO + (Off)idx), ev + od, L::w(ia));
+      Store<S>::st_w(dst + ((Off)L::opp(ia) * NO + (Off)idx), ev - od, L::w(ia));
     }
   }
   u_out[idx] = u0;
-  u_out[N + idx] = u1;
-  if (DIM == 3) u_out[2 * N + idx] = u2;
+  u_out[NO + (Off)idx] = u1;
+  if (DIM == 3) u_out[2 * NO + (Off)idx] = u2;
 }
 
 template <class L, int S>
@@ -276,10 +283,14 @@ cudaError_t launch_hydro_t(int mode, const KParams &P, const void *src, void *ds
   using T = typename Store<S>::T;
   dim3 block(TT::X, TT::Y, TT::Z);
   dim3 grid((P.nx + TT::X - 1) / TT::X, (P.ny + TT::Y - 1) / TT::Y, (P.nz + TT::Z - 1) / TT::Z);
-  if (mode == kStep)
-    k_hydro<L, S, kStep><<<grid, block, 0, s>>>(P, (const T *)src, (T *)dst, phi, frep, u, pstar, reset);
-  else
-    k_hydro<L, S, kMoments><<<grid, block, 0, s>>>(P, (const T *)src, (T *)dst, phi, frep, u, pstar, reset);
+  const bool i32 = (long long)L::Q * P.N <= (1LL << 32);  // largest offset Q N - 1 fits an unsigned
+  if (mode == kStep) {
+    if (i32) k_hydro<L, S, kStep, true><<<grid, block, 0, s>>>(P, (const T *)src, (T *)dst, phi, frep, u, pstar, reset);
+    else k_hydro<L, S, kStep, false><<<grid, block, 0, s>>>(P, (const T *)src, (T *)dst, phi, frep, u, pstar, reset);
+  } else {
+    if (i32) k_hydro<L, S, kMoments, true><<<grid, block, 0, s>>>(P, (const T *)src, (T *)dst, phi, frep, u, pstar, reset);
+    else k_hydro<L, S, kMoments, false><<<grid, block, 0, s>>>(P, (const T *)src, (T *)dst, phi, frep, u, pstar, reset);
+  }
   return cudaGetLastError();
 }
 
