@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(Tile<L::D>::X * Tile<L::D>::Y * Tile<L::D>::Z,
 k_hydro(const KParams P, const typename Store<S>::T *__restrict__ src, typename Store<S>::T *__restrict__ dst,
         const int32_t *__restrict__ phi, const float4 *__restrict__ frep, float *__restrict__ u_out,
         float *__restrict__ ps_out, int *__restrict__ reset) {
+  pdl_enter();
   constexpr int DIM = L::D;
   using SL = typename StencilOf<DIM>::type;
   using TT = Tile<DIM>;
@@ -284,14 +285,13 @@ cudaError_t launch_hydro_t(int mode, const KParams &P, const void *src, void *ds
   dim3 block(TT::X, TT::Y, TT::Z);
   dim3 grid((P.nx + TT::X - 1) / TT::X, (P.ny + TT::Y - 1) / TT::Y, (P.nz + TT::Z - 1) / TT::Z);
   const bool i32 = (long long)L::Q * P.N <= (1LL << 32);  // largest offset Q N - 1 fits an unsigned
-  if (mode == kStep) {
-    if (i32) k_hydro<L, S, kStep, true><<<grid, block, 0, s>>>(P, (const T *)src, (T *)dst, phi, frep, u, pstar, reset);
-    else k_hydro<L, S, kStep, false><<<grid, block, 0, s>>>(P, (const T *)src, (T *)dst, phi, frep, u, pstar, reset);
-  } else {
-    if (i32) k_hydro<L, S, kMoments, true><<<grid, block, 0, s>>>(P, (const T *)src, (T *)dst, phi, frep, u, pstar, reset);
-    else k_hydro<L, S, kMoments, false><<<grid, block, 0, s>>>(P, (const T *)src, (T *)dst, phi, frep, u, pstar, reset);
-  }
-  return cudaGetLastError();
+  const T *a = (const T *)src;
+  T *b = (T *)dst;
+  if (mode == kStep)
+    return i32 ? launch_pdl(k_hydro<L, S, kStep, true>, grid, block, 0, s, P, a, b, phi, frep, u, pstar, reset)
+               : launch_pdl(k_hydro<L, S, kStep, false>, grid, block, 0, s, P, a, b, phi, frep, u, pstar, reset);
+  return i32 ? launch_pdl(k_hydro<L, S, kMoments, true>, grid, block, 0, s, P, a, b, phi, frep, u, pstar, reset)
+             : launch_pdl(k_hydro<L, S, kMoments, false>, grid, block, 0, s, P, a, b, phi, frep, u, pstar, reset);
 }
 
 template <class L>

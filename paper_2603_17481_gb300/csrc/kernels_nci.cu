@@ -80,6 +80,7 @@ __device__ __forceinline__ void tile_of(int tile, int gtx, int gty, int &bx, int
 __global__ void __launch_bounds__(NciGeom<2>::NT)
 k_nci_normals2(const KParams P, const int32_t *__restrict__ phi, float4 *__restrict__ nrm,
                const int *__restrict__ tiles, const int *__restrict__ ntiles, int total, int gtx, int gty) {
+  pdl_enter();
   using G = NciGeom<2>;
   using SL = StencilOf<2>::type;
   const int n = tiles ? *ntiles : total;
@@ -126,6 +127,7 @@ __global__ void __launch_bounds__(kNrmThreads)
 k_nci_normals3(const KParams P, const int32_t *__restrict__ phi, float4 *__restrict__ nrm, float4 *__restrict__ frep,
                const int *__restrict__ tiles, const int *__restrict__ ntiles, int total, int gtx, int gty,
                const NciAux aux) {
+  pdl_enter();
   using G = NciGeom<3>;
   using SL = StencilOf<3>::type;
   using B = NrmBox;
@@ -245,6 +247,7 @@ __global__ void __launch_bounds__(128)
 k_nci_prefilter(const KParams P, const uint4 *__restrict__ bricks, const unsigned char *__restrict__ flags,
                 const int *__restrict__ tiles, const int *__restrict__ ntiles, int *__restrict__ scan_tiles,
                 int *__restrict__ nscan, int gtx, int gty) {
+  pdl_enter();
   constexpr int RX = 10, RY = 4, RZ = 3, NR = RX * RY * RZ;
   __shared__ float s_r[6][NR];
   __shared__ float s_b[48];
@@ -310,6 +313,7 @@ k_nci_scan(const KParams P, const NciTable T, const int32_t *__restrict__ phi, c
            float4 *__restrict__ frep, int32_t *__restrict__ partner, int debug, const int *__restrict__ tiles,
            const int *__restrict__ ntiles, int total, int gtx, int gty, unsigned char *__restrict__ flags,
            const int *__restrict__ listed, const int *__restrict__ nlisted) {
+  pdl_enter();
   using G = NciGeom<DIM>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int32_t *s_phi = reinterpret_cast<int32_t *>(smem_raw);
@@ -671,22 +675,24 @@ static cudaError_t launch_nci_dim(const KParams &P, const NciTable &T, const int
   const bool pre = DIM == 3 && aux && tiles && aux->bricks && nci_aux_applies(DIM, P);
   const NciAux none{};
   if constexpr (DIM == 2) {
-    k_nci_normals2<<<blocks, block, 0, s>>>(P, phi, nrm, tiles, ntiles, total, gtx, gty);
+    cudaError_t e2 = launch_pdl(k_nci_normals2, dim3(blocks), block, 0, s, P, phi, nrm, tiles, ntiles, total, gtx, gty);
+    if (e2 != cudaSuccess) return e2;
   } else {
     // one block per half tile, at most 16 blocks per resident scan block (grid-stride beyond)
     const int nb = 2 * total < 16 * list_blocks ? 2 * total : 16 * list_blocks;
-    k_nci_normals3<<<nb, kNrmThreads, 0, s>>>(P, phi, nrm, frep, tiles, ntiles, total, gtx, gty, pre ? *aux : none);
+    cudaError_t e3 = launch_pdl(k_nci_normals3, dim3(nb), dim3(kNrmThreads), 0, s, P, phi, nrm, frep, tiles, ntiles, total,
+                                gtx, gty, pre ? *aux : none);
+    if (e3 != cudaSuccess) return e3;
   }
   if (!pre) {
-    k_nci_scan<DIM><<<blocks, block, G::smem, s>>>(P, T, phi, nrm, frep, partner, debug, tiles, ntiles, total, gtx,
-                                                   gty, nullptr, nullptr, nullptr);
-    return cudaGetLastError();
+    return launch_pdl(k_nci_scan<DIM>, dim3(blocks), block, G::smem, s, P, T, phi, nrm, frep, partner, debug, tiles,
+                      ntiles, total, gtx, gty, nullptr, nullptr, nullptr);
   }
-  k_nci_prefilter<<<16 * list_blocks, 128, 0, s>>>(P, aux->bricks, aux->flags, tiles, ntiles, aux->scan_tiles,
-                                                   aux->nscan, gtx, gty);
-  k_nci_scan<DIM><<<blocks, block, G::smem, s>>>(P, T, phi, nrm, frep, partner, debug, aux->scan_tiles, aux->nscan,
-                                                 total, gtx, gty, aux->flags, tiles, ntiles);
-  return cudaGetLastError();
+  e = launch_pdl(k_nci_prefilter, dim3(16 * list_blocks), dim3(128), 0, s, P, (const uint4 *)aux->bricks,
+                 (const unsigned char *)aux->flags, tiles, ntiles, aux->scan_tiles, aux->nscan, gtx, gty);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(k_nci_scan<DIM>, dim3(blocks), block, G::smem, s, P, T, phi, nrm, frep, partner, debug,
+                    (const int *)aux->scan_tiles, (const int *)aux->nscan, total, gtx, gty, aux->flags, tiles, ntiles);
 }
 
 cudaError_t launch_nci(int dim, const KParams &P, const NciTable &T, const int32_t *phi, float4 *nrm, float4 *frep,

@@ -130,6 +130,7 @@ template <int DIM>
 __global__ void __launch_bounds__(PhaseGeom<DIM>::NT)
 k_phase(const KParams P, const int32_t *__restrict__ phi, const float *__restrict__ u,
         int32_t *__restrict__ phi_out, int *__restrict__ tiles, int *__restrict__ ntiles) {
+  pdl_enter();
   using G = PhaseGeom<DIM>;
   using SL = typename StencilOf<DIM>::type;
   __shared__ int32_t s_phi[G::NB];
@@ -279,6 +280,7 @@ __device__ __forceinline__ float minmod_f(float a, float b) {
 __global__ void __launch_bounds__(Phase3::NT, LBM_PHASE_MINB)
 k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restrict__ u,
          int32_t *__restrict__ phi_out, int *__restrict__ tiles, int *__restrict__ ntiles, const int zc) {
+  pdl_enter();
   using G = Phase3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float *RZ = reinterpret_cast<float *>(smem_raw);           // [2][NP]
@@ -538,8 +540,7 @@ static cudaError_t launch_phase_dim(const KParams &P, const int32_t *phi, const 
   using G = PhaseGeom<DIM>;
   dim3 block(G::TX, G::TY, G::TZ);
   dim3 grid((P.nx + G::TX - 1) / G::TX, (P.ny + G::TY - 1) / G::TY, (P.nz + G::TZ - 1) / G::TZ);
-  k_phase<DIM><<<grid, block, 0, s>>>(P, phi, u, phi_out, tiles, ntiles);
-  return cudaGetLastError();
+  return launch_pdl(k_phase<DIM>, grid, block, 0, s, P, phi, u, phi_out, tiles, ntiles);
 }
 
 // Raises k_phase3's dynamic shared-memory limit once. Context creation calls this, so that the
@@ -578,8 +579,7 @@ static cudaError_t launch_phase3(const KParams &P, const int32_t *phi, const flo
   if (e != cudaSuccess) return e;
   const int zc = phase3_zc(P.nx, P.ny, P.nz);
   dim3 grid((P.nx + G::TX - 1) / G::TX, (P.ny + G::TY - 1) / G::TY, (P.nz + zc - 1) / zc);
-  k_phase3<<<grid, dim3(32, G::TY), G::smem, s>>>(P, phi, u, phi_out, tiles, ntiles, zc);
-  return cudaGetLastError();
+  return launch_pdl(k_phase3, grid, dim3(32, G::TY), G::smem, s, P, phi, u, phi_out, tiles, ntiles, zc);
 }
 
 cudaError_t launch_phase(int dim, const KParams &P, const int32_t *phi, const float *u, int32_t *phi_out,

@@ -1,9 +1,27 @@
 // launch.h -- host-side launchers of the liblbm kernels (internal to the library).
 #pragma once
 
+#include <utility>
+
 #include "lbm_device.cuh"
 
 namespace lbm {
+
+// Launches a step kernel with programmatic stream serialization (see pdl_enter).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args &&...args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Window offsets of the near-contact search, sorted by (|r|^2, canonical index), passed by value.
 struct NciTable {

@@ -131,6 +131,15 @@ __host__ __device__ __forceinline__ int wrapi(int a, int n) {
   a %= n;
   return a < 0 ? a + n : a;
 }
+// Programmatic dependent launch. The step kernels are launched so that each may be scheduled while
+// the kernel before it on the stream finishes; the first thing each does is wait for that grid to
+// complete (its memory operations done and visible), so nothing is read or written earlier. It then
+// lets the next step kernel be scheduled. Launched without the attribute, both are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Periodic wrap with a fast path for in-range coordinates.
 __device__ __forceinline__ int wrapn(int a, int n) { return (unsigned)a < (unsigned)n ? a : wrapi(a, n); }
 
