@@ -185,7 +185,7 @@ def centroids(cfg, phi):
 
 def make_workload(Q=19):
     from paper_2603_17481_gb300 import workloads as W
-    cfg, phi, u = W.c3_head_on_3d(Q=Q)
+    cfg, phi, u = W.droplets_head_on_3d(Q=Q)
     phi = W.to_q30_grid(phi)
     return cfg, phi, u
 
@@ -397,11 +397,11 @@ def run_sweep(args, world, rank, local):
 
     torch.cuda.set_device(local)
     lbm_build.build()
-    cfgs = W.c4_sweep(args.cases, seed=17481 + rank)
+    cfgs = W.collision_sweep(args.cases, seed=17481 + rank)
     stream = torch.cuda.Stream()
     sims, m0 = [], []
     for cfg in cfgs:
-        phi, u = W.c4_fields(cfg)
+        phi, u = W.sweep_case_fields(cfg)
         s = B.Lbm(cfg, stream=stream.cuda_stream)
         s.init_fields(phi, u)
         m0.append(s.mass()[0])
@@ -526,8 +526,8 @@ def run_swarm(args, world, rank, local):
 
     torch.cuda.set_device(local)
     lbm_build.build()
-    cfg, cs, rs = W.c5_swarm(L=args.swarm_L, nb=args.swarm_bubbles, seed=17481 + rank, gap_eps=args.swarm_gap)
-    phi, u = W.c5_fields(cfg, cs, rs)
+    cfg, cs, rs = W.bubble_swarm(L=args.swarm_L, nb=args.swarm_bubbles, seed=17481 + rank, gap_eps=args.swarm_gap)
+    phi, u = W.bubble_swarm_fields(cfg, cs, rs)
     N = W.ncells(cfg)
     L = cfg["nx"]
     nb0 = count_bubbles((phi < 0.5).reshape(L, L, L))
@@ -627,7 +627,7 @@ def run_selftune(args, world, rank, local):
     stream = torch.cuda.Stream()
     sims = []
     for cfg in cfgs:
-        phi, u = W.c4_fields(cfg)
+        phi, u = W.sweep_case_fields(cfg)
         s = B.Lbm(cfg, stream=stream.cuda_stream)
         s.init_fields(phi, u)
         sims.append(s)

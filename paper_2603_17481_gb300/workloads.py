@@ -82,7 +82,7 @@ def droplet_fields(cfg, centers, radii, velocities, bubbles=False):
 # The five workloads (sizes, lattices, physical parameters) and their initial fields.
 # --------------------------------------------------------------------------------------------
 
-def c1_head_on_2d():
+def droplets_head_on_2d():
     """2D head-on collision, 128x64 D2Q9, R = 16, centres 40 apart, +-0.02, density ratio 1."""
     cfg = base_config(2, 128, 64, 1, 9, steps=200)
     phi, u = droplet_fields(cfg, [(43.5, 31.5, 0.0), (83.5, 31.5, 0.0)], [16.0, 16.0],
@@ -90,7 +90,7 @@ def c1_head_on_2d():
     return cfg, phi, u
 
 
-def c2_offcentre_3d(seed=17481, nx=128, ny=64, nz=64, R=12.0):
+def droplets_offcentre_3d(seed=17481, nx=128, ny=64, nz=64, R=12.0):
     """3D collision, 128x64x64 D3Q19, R = 12, separation 2R + 8 along x, impact offset
     b ~ U(0, 1) * R along y, relative speed 0.04, density ratio 10."""
     cfg = base_config(3, nx, ny, nz, 19, rho_g=0.1, steps=2000)
@@ -104,7 +104,7 @@ def c2_offcentre_3d(seed=17481, nx=128, ny=64, nz=64, R=12.0):
     return cfg, phi, u
 
 
-def c3_head_on_3d(nx=256, ny=128, nz=128, R=24.0, Q=19):
+def droplets_head_on_3d(nx=256, ny=128, nz=128, R=24.0, Q=19):
     """3D head-on collision, 256x128x128 D3Q19, R = 24, separation 2R + 8, speed 0.04, ratio 100."""
     cfg = base_config(3, nx, ny, nz, Q, rho_g=0.01, steps=5000)
     cx, cy, cz = (nx - 1) / 2.0, (ny - 1) / 2.0, (nz - 1) / 2.0
@@ -118,14 +118,14 @@ def c3_head_on_3d(nx=256, ny=128, nz=128, R=24.0, Q=19):
 SWEEP_GRIDS = (48, 64, 80, 96)
 
 
-def c4_sweep(n=512, seed=17481, sigma=1e-3, we_min=1.0, we_max=100.0, grids=SWEEP_GRIDS):
+def collision_sweep(n=512, seed=17481, sigma=1e-3, we_min=1.0, we_max=100.0, grids=SWEEP_GRIDS):
     """Parameter sets of the batched sweep: ``n`` independent 3D D3Q19 collisions, density ratio 10.
 
     Case i draws from ``default_rng(seed + i)``: its cubic grid edge L from ``grids``, R = L / 6, a
     Weber number We = rho_l U^2 (2R) / sigma log-uniform in [we_min, we_max], set through the
     relative speed U = sqrt(We sigma / (rho_l 2R)) (U <= 0.08 for sigma = 1e-3), and an impact
     offset b ~ U(0, 1) 2R along y. A_rep = sigma; viscosities as in the other collisions. The
-    droplets start 2R + 8 apart along x, moving at -+U/2. Fields come from ``c4_fields``.
+    droplets start 2R + 8 apart along x, moving at -+U/2. Fields come from ``sweep_case_fields``.
     """
     out = []
     for i in range(n):
@@ -151,7 +151,7 @@ def selftune_cases(diameters=(24, 32, 48), sigmas=(0.005, 0.01, 0.02), ratios=(0
     Each case is a periodic box (2D + 24) x (D + 16)^2 with two droplets of diameter D, 2R + 8 apart
     along x, approaching at the relative speed U = sqrt(We sigma / (rho_l D)) with We = 4.6 (the
     head-on experiment of Sec. 3.1); density ratio 10 and the other parameters as in the
-    collisions above. Fields come from ``c4_fields``. (The diameter is stored as ``diameter``: ``D``
+    collisions above. Fields come from ``sweep_case_fields``. (The diameter is stored as ``diameter``: ``D``
     is the phase-field mobility.)
     """
     out = []
@@ -171,7 +171,7 @@ def selftune_cases(diameters=(24, 32, 48), sigmas=(0.005, 0.01, 0.02), ratios=(0
     return out
 
 
-def c4_fields(cfg):
+def sweep_case_fields(cfg):
     """phi (rounded to the 2^-30 grid) and u of one sweep case."""
     phi, u = droplet_fields(cfg, cfg["centers"], [cfg["R"], cfg["R"]], cfg["velocities"])
     return to_q30_grid(phi), u
@@ -198,7 +198,7 @@ def swarm_centres(L, nb, rmin, rmax, gap, seed=17481, max_tries=2_000_000):
     return np.array(cs), np.array(rs)
 
 
-def c5_swarm(L=512, nb=1500, seed=17481, rmin=8.0, rmax=12.0, gap_eps=2.0):
+def bubble_swarm(L=512, nb=1500, seed=17481, rmin=8.0, rmax=12.0, gap_eps=2.0):
     """Buoyant bubble swarm, L^3 D3Q19, nb bubbles R ~ U[8, 12], ratio 100, g = 1e-6, sigma = 0.01.
 
     Bubble surfaces start at least gap_eps * eps apart, so that their diffuse interfaces do not
@@ -212,7 +212,7 @@ def c5_swarm(L=512, nb=1500, seed=17481, rmin=8.0, rmax=12.0, gap_eps=2.0):
     return cfg, cs, rs
 
 
-def c5_fields(cfg, cs, rs, cut=4.0):
+def bubble_swarm_fields(cfg, cs, rs, cut=4.0):
     """phi of the bubble swarm (gas inside, phi = 0), u = 0, built box by box.
 
     Each bubble's profile (1 + tanh(2 (R - r) / eps)) / 2 is evaluated only within a cube of half

@@ -25,7 +25,7 @@ def _small_cases():
     """Uneven small cases, 2D and 3D, both stencil families, near-contact on and off."""
     cases = []
     for i, L in enumerate((24, 40, 32, 20, 36)):
-        cfg = W.c4_sweep(1, seed=100 + i, grids=(L,))[0]
+        cfg = W.collision_sweep(1, seed=100 + i, grids=(L,))[0]
         if i == 3:
             cfg["nci_on"] = 0
         cases.append(cfg)
@@ -33,7 +33,7 @@ def _small_cases():
     c2.update(centers=[(24.0, 19.3, 0.0), (45.5, 18.6, 0.0)], R=8.0,
               velocities=[(0.02, 0.0, 0.0), (-0.02, 0.0, 0.0)])
     cases.append(c2)
-    c27 = W.c4_sweep(1, seed=7, grids=(28,))[0]
+    c27 = W.collision_sweep(1, seed=7, grids=(28,))[0]
     c27["Q"] = 27
     cases.append(c27)
     return cases
@@ -48,7 +48,7 @@ def test_batch_matches_per_case_steps(nstreams):
     cases = _small_cases()
     single, batched = [], []
     for cfg in cases:
-        phi, u = W.c4_fields(cfg)
+        phi, u = W.sweep_case_fields(cfg)
         for lst in (single, batched):
             s = B.Lbm(cfg)
             s.init_fields(phi, u)
@@ -71,17 +71,17 @@ def test_batch_matches_per_case_steps(nstreams):
 
 def test_batch_case_against_oracle():
     """A 40^3 sweep case advanced 20 steps inside a batch of three against the FP64 oracle."""
-    cfgs = [W.c4_sweep(1, seed=s, grids=(L,))[0] for s, L in ((3, 40), (4, 24), (5, 32))]
+    cfgs = [W.collision_sweep(1, seed=s, grids=(L,))[0] for s, L in ((3, 40), (4, 24), (5, 32))]
     sims = []
     for cfg in cfgs:
-        phi, u = W.c4_fields(cfg)
+        phi, u = W.sweep_case_fields(cfg)
         s = B.Lbm(cfg)
         s.init_fields(phi, u)
         sims.append(s)
     batch = B.LbmBatch(sims, nstreams=2)
     batch.step(20)
     cfg = cfgs[0]
-    phi, u = W.c4_fields(cfg)
+    phi, u = W.sweep_case_fields(cfg)
     P = O.make_params(cfg)
     f = O.init(P, phi, u)
     fo, pho, _ = O.step(P, f, phi, 20)
@@ -95,8 +95,8 @@ def test_batch_case_against_oracle():
 
 
 def test_batch_rejects_bad_contexts():
-    cfg = W.c4_sweep(1, seed=1, grids=(20,))[0]
-    phi, u = W.c4_fields(cfg)
+    cfg = W.collision_sweep(1, seed=1, grids=(20,))[0]
+    phi, u = W.sweep_case_fields(cfg)
     checked = B.Lbm(cfg, mass_check_every=10)
     checked.init_fields(phi, u)
     fresh = B.Lbm(cfg)  # never initialised

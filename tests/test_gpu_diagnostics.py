@@ -192,8 +192,8 @@ def test_full_size_swarm_listed_pass_and_mass():
     with surface gaps of eps so that films exist from the start: after 10 steps the sum of the
     fixed-point phi is unchanged, and the per-step near-contact pass over the listed tiles (with the
     brick prefilter) finds exactly the partners and forces of the pass over every tile."""
-    cfg, cs, rs = W.c5_swarm(gap_eps=1.0)
-    phi, u = W.c5_fields(cfg, cs, rs)
+    cfg, cs, rs = W.bubble_swarm(gap_eps=1.0)
+    phi, u = W.bubble_swarm_fields(cfg, cs, rs)
     sim = B.Lbm(cfg)
     sim.init_fields(phi, u)
     del phi, u

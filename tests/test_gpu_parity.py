@@ -81,9 +81,9 @@ def test_single_step_identical_input(dim, Q, shape, seed, store):
     assert np.round(phg * 2 ** 30).sum() == m0  # exact fixed-point conservation
 
 
-def test_c1_head_on_2d_200_steps():
+def test_head_on_2d_128x64_200_steps():
     """2D head-on collision (128x64 D2Q9), 200 steps: max|dphi| <= 1e-5, max|du| <= 1e-6."""
-    cfg, phi, u = W.c1_head_on_2d()
+    cfg, phi, u = W.droplets_head_on_2d()
     phi = W.to_q30_grid(phi)
     P = O.make_params(cfg)
     f = O.init(P, phi, u)
@@ -101,10 +101,10 @@ def _check_traj(phg, pho, ug, uo, tphi=1e-5, tu=1e-6):
     assert dphi <= tphi and du <= tu, f"max|dphi|={dphi:.3e} (tol {tphi}), max|du|={du:.3e} (tol {tu})"
 
 
-def test_c1_contact_phase_400_steps():
+def test_head_on_2d_128x64_contact_400_steps():
     """The same collision through its near-contact phase (the repulsion switches on near step
     250): partners compared at step 400, and fields within 1e-5 (phi) / 1e-6 (u)."""
-    cfg, phi, u = W.c1_head_on_2d()
+    cfg, phi, u = W.droplets_head_on_2d()
     phi = W.to_q30_grid(phi)
     P = O.make_params(cfg)
     f = O.init(P, phi, u)
@@ -120,10 +120,10 @@ def test_c1_contact_phase_400_steps():
     _check_traj(phg, pho, ug, uo)
 
 
-def test_c2_offcentre_3d_200_steps():
+def test_offcentre_3d_128x64x64_200_steps():
     """3D off-centre collision (128x64x64 D3Q19, ratio 10, seeded impact offset), 200 steps:
     max|dphi| <= 1e-5, max|du| <= 1e-6."""
-    cfg, phi, u = W.c2_offcentre_3d()
+    cfg, phi, u = W.droplets_offcentre_3d()
     phi = W.to_q30_grid(phi)
     P = O.make_params(cfg)
     f = O.init(P, phi, u)
@@ -159,7 +159,7 @@ def test_d3q27_collision_200_steps():
 def test_half_precision_store_phi_error_and_mass(store, tol):
     """Populations stored as FP16/BF16 (f/w_i) with FP32 arithmetic, ratio-100 collision
     (128x64x64, R = 12), 200 steps: phi error against the FP64 oracle below tol, phi mass exact."""
-    cfg, phi, u = W.c3_head_on_3d(nx=128, ny=64, nz=64, R=12.0)
+    cfg, phi, u = W.droplets_head_on_3d(nx=128, ny=64, nz=64, R=12.0)
     phi = W.to_q30_grid(phi)
     P = O.make_params(cfg)
     f = O.init(P, phi, u)
@@ -233,10 +233,10 @@ def test_step_before_init_and_nan_detection():
     assert ei.value.code == B.LBM_ERR_UNSTABLE
 
 
-def test_full_size_single_step_c3():
+def test_full_size_single_step_256x128x128():
     """The benchmark's launch configuration (256x128x128 D3Q19, ratio 100): one step from the
     initial state against the oracle on the whole grid."""
-    cfg, phi, u = W.c3_head_on_3d()
+    cfg, phi, u = W.droplets_head_on_3d()
     phi = W.to_q30_grid(phi)
     P = O.make_params(cfg)
     f = O.init(P, phi, u)
@@ -250,9 +250,9 @@ def test_full_size_single_step_c3():
 
 
 @pytest.mark.slow
-def test_c2_centroids_after_2000_steps():
+def test_offcentre_3d_centroids_after_2000_steps():
     """Droplet centroids (phi-weighted, per half-domain in x) within 0.05 cells after 2000 steps."""
-    cfg, phi, u = W.c2_offcentre_3d()
+    cfg, phi, u = W.droplets_offcentre_3d()
     phi = W.to_q30_grid(phi)
     P = O.make_params(cfg)
     f = O.init(P, phi, u)

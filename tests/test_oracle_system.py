@@ -67,7 +67,7 @@ def test_head_on_collision_mirror_symmetry_and_mass(orc):
     """The 2D head-on collision (droplets R = 16 at x = 43.5 and 83.5, +-0.02) is symmetric under
     x -> 127 - x (u_x odd) and y -> 63 - y (u_y odd): after 120 steps both symmetries hold to
     1e-12, and sum(phi) is conserved to 1e-12 relative."""
-    cfg, phi, u = W.c1_head_on_2d()
+    cfg, phi, u = W.droplets_head_on_2d()
     P = orc.make_params(cfg)
     f = orc.init(P, phi, u)
     f, ph, ul = orc.step(P, f, phi, 120)

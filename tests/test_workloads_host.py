@@ -13,7 +13,7 @@ import bench  # noqa: E402
 
 
 def test_sweep_parameters():
-    cases = W.c4_sweep(512)
+    cases = W.collision_sweep(512)
     assert len(cases) == 512
     assert {c["nx"] for c in cases} == set(W.SWEEP_GRIDS)
     for c in cases:
@@ -26,18 +26,18 @@ def test_sweep_parameters():
         (x0, y0, _), (x1, y1, _) = c["centers"]
         assert math.isclose(x1 - x0, 2 * R + 8) and math.isclose(y1 - y0, c["impact_offset"])
     # reproducible from the seed
-    assert W.c4_sweep(3, seed=5) == W.c4_sweep(3, seed=5)
+    assert W.collision_sweep(3, seed=5) == W.collision_sweep(3, seed=5)
 
 
 def test_swarm_fields_match_all_cells_profile():
-    cfg, cs, rs = W.c5_swarm(L=80, nb=8, seed=4)
+    cfg, cs, rs = W.bubble_swarm(L=80, nb=8, seed=4)
     assert len(cs) == 8
     for i in range(len(cs)):
         for j in range(i):
             d = cs[i] - cs[j]
             d -= 80 * np.round(d / 80)
             assert np.linalg.norm(d) >= rs[i] + rs[j] + 2 * cfg["eps"]
-    phi, u = W.c5_fields(cfg, cs, rs)
+    phi, u = W.bubble_swarm_fields(cfg, cs, rs)
     ref, _ = W.droplet_fields(cfg, cs, rs, [(0, 0, 0)] * len(cs), bubbles=True)
     # each truncated profile tail is below 1.2e-7, so the fields differ by less than that per bubble
     assert np.max(np.abs(phi - ref)) < 1.2e-7 * len(cs)
@@ -61,8 +61,8 @@ def test_count_bubbles_periodic():
 
 
 def test_count_bubbles_of_generated_swarm():
-    cfg, cs, rs = W.c5_swarm(L=96, nb=20, seed=9)
-    phi, _ = W.c5_fields(cfg, cs, rs)
+    cfg, cs, rs = W.bubble_swarm(L=96, nb=20, seed=9)
+    phi, _ = W.bubble_swarm_fields(cfg, cs, rs)
     n, vols = bench.count_bubbles((phi < 0.5).reshape(96, 96, 96), volumes=True)
     assert n == len(cs) == len(vols)
     # each component's volume is its sphere's to within the lattice sampling of the surface
@@ -83,7 +83,7 @@ def test_workload_extras_do_not_shadow_parameters():
     none of them may overwrite a parameter such as the mobility D."""
     import oracle as O
     base = W.base_config(3, 8, 8, 8, 19)
-    for cfg in W.selftune_cases()[:3] + W.c4_sweep(3):
+    for cfg in W.selftune_cases()[:3] + W.collision_sweep(3):
         assert cfg["D"] == base["D"] and cfg["p"] == base["p"] and cfg["eps"] == base["eps"]
         extra = set(cfg) - set(base)
         assert not extra & set(O._FIELDS)
@@ -96,4 +96,4 @@ def test_kernels_per_step():
     assert bench.kernels_per_step(W.base_config(3, 37, 21, 13, 19)) == 4
     assert bench.kernels_per_step(W.base_config(3, 64, 48, 40, 19, nci_on=0)) == 2
     assert bench.kernels_per_step(W.base_config(2, 128, 64, 1, 9)) == 4
-    assert all(bench.kernels_per_step(c) == 5 for c in W.c4_sweep(8))
+    assert all(bench.kernels_per_step(c) == 5 for c in W.collision_sweep(8))
