@@ -265,10 +265,21 @@ struct Phase3 {
 
 __device__ __forceinline__ float s141(float a, float b, float c) { return a + 4.0f * b + c; }
 
+// minmod(a, b): the argument of smaller magnitude when both have the same sign, else 0. a b cannot
+// underflow here (nonzero phi differences are at least 2^-30), so the sign test is exact.
 __device__ __forceinline__ float minmod_f(float a, float b) {
-  if (a > 0.0f && b > 0.0f) return fminf(a, b);
-  if (a < 0.0f && b < 0.0f) return fmaxf(a, b);
-  return 0.0f;
+  return a * b > 0.0f ? copysignf(fminf(fabsf(a), fabsf(b)), a) : 0.0f;
+}
+
+// Upwind MUSCL state at the face between cells p and p + e (Eqs. 30-34) from phi at p - e, p, p + e,
+// p + 2e: phi(p) + minmod(phi(p) - phi(p-e), phi(p+e) - phi(p)) / 2 when u_f >= 0, else
+// phi(p+e) - minmod(phi(p+e) - phi(p), phi(p+2e) - phi(p+e)) / 2. The triple (L, C, R) is selected
+// first and one limiter evaluated: minmod(-a, -b) = -minmod(a, b) makes C + minmod(C - L, R - C) / 2
+// with (L, C, R) = (phi(p+2e), phi(p+e), phi(p)) equal to the second form, bit for bit.
+__device__ __forceinline__ float upwind_f(float uf, float vm, float v0, float v1, float vp) {
+  const bool pos = uf >= 0.0f;
+  const float L = pos ? vm : vp, C = pos ? v0 : v1, R = pos ? v1 : v0;
+  return C + 0.5f * minmod_f(C - L, R - C);
 }
 
 // Resident k_phase3 blocks per SM its registers are sized for: 4 (64 registers) measured 0.110 ms on
@@ -482,7 +493,7 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
                                 AXZ[q + G::QX] + AXZ[q + G::QX + 1]);
           const float vm = p0[c - 1], v0 = p0[c], v1 = p0[c + 1], vp = p0[c + 2];
           const float uf = 0.5f * (UX[t] + UX[t + 1]);
-          const float up = uf >= 0.0f ? v0 + 0.5f * minmod_f(v0 - vm, v1 - v0) : v1 - 0.5f * minmod_f(v1 - v0, vp - v1);
+          const float up = upwind_f(uf, vm, v0, v1, vp);
           TXF[t] = __float2int_rn(kQ30 * fmaf(Dx, di, fmaf(k3s, cs, uf * up)));
         }
         for (int t = tid; t < G::NFY; t += G::NT) {
@@ -494,7 +505,7 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
                                 AYZ[q + 1] + AYZ[q + 1 + G::QX]);
           const float vm = p0[c - G::PX], v0 = p0[c], v1 = p0[c + G::PX], vp = p0[c + 2 * G::PX];
           const float uf = 0.5f * (UY[(ly + 1) * G::TX + lx] + UY[(ly + 2) * G::TX + lx]);
-          const float up = uf >= 0.0f ? v0 + 0.5f * minmod_f(v0 - vm, v1 - v0) : v1 - 0.5f * minmod_f(v1 - v0, vp - v1);
+          const float up = upwind_f(uf, vm, v0, v1, vp);
           TYF[t] = __float2int_rn(kQ30 * fmaf(Dy, di, fmaf(k3s, cs, uf * up)));
         }
       }
@@ -505,7 +516,7 @@ k_phase3(const KParams P, const int32_t *__restrict__ phi, const float *__restri
         const float vm = PF[s4km * G::NP + c], v0 = p0[c], v1 = PF[s4k1 * G::NP + c], vp = PF[s4k2 * G::NP + c];
         const float cs = ASXY[(k & 1) * G::NC + tid] + ASXY[((k + 1) & 1) * G::NC + tid];
         const float uf = 0.5f * (UZ[(k & 1) * G::NC + tid] + UZ[((k + 1) & 1) * G::NC + tid]);
-        const float up = uf >= 0.0f ? v0 + 0.5f * minmod_f(v0 - vm, v1 - v0) : v1 - 0.5f * minmod_f(v1 - v0, vp - v1);
+        const float up = upwind_f(uf, vm, v0, v1, vp);
         TZF[((k + 1) & 1) * G::NC + tid] = __float2int_rn(kQ30 * fmaf(D, di, fmaf(k3s, cs, uf * up)));
       }
     }
