@@ -194,11 +194,12 @@ void lbm_batch_destroy(lbm_batch *b);
 int lbm_synchronize(lbm_ctx *ctx);
 
 /* Per-kernel timing with CUDA events on the context stream (enable = 1 starts a fresh tally of every
- * kind, enable = 0 stops). Each timed pass records two events on the stream, which adds a little
- * time between kernels. */
+ * kind, enable = 0 stops). Synchronises the stream first. Each timed pass records two events on the
+ * stream, which adds a little time between kernels (and ends the launch overlap between the step
+ * kernels around it). Null ctx: LBM_ERR_ARG; a CUDA failure of the synchronisation: LBM_ERR_CUDA. */
 int lbm_profile(lbm_ctx *ctx, int enable);
-/* As lbm_profile, timing only the kinds whose bit (1u << kind) is set in mask; mask = 0 stops. Bits
- * of kinds beyond LBM_K_COUNT are ignored. */
+/* As lbm_profile, timing only the kinds whose bit (1u << kind, kind an lbm_kernel_kind) is set in
+ * mask; mask = 0 stops. Bits of kinds beyond LBM_K_COUNT are ignored. Same errors as lbm_profile. */
 int lbm_profile_kinds(lbm_ctx *ctx, unsigned mask);
 /* Accumulated device milliseconds and kernel launch counts per lbm_kernel_kind (arrays of
  * LBM_K_COUNT; either may be NULL). A pass of several kernels counts each of them: the near-contact
