@@ -1,10 +1,13 @@
 // kernels_nci.cu -- near-contact interaction (Sec. 2.3): interfacial gate (Eqs. 58-59), bounded
 // window pairing (Eqs. 60-65), closed-form proximity indicator and repulsive force (Eqs. 66-73).
 //
-// Two passes over the tiles that hold an interfacial (gated) cell, as listed by the phase-field
-// kernel of the previous step (or over every tile for the diagnostic read-back):
-//   k_nci_normals  the normal n = grad(phi) / (|grad(phi)| + eps_n) of every gated cell (Eq. 57,
-//                  isotropic gradient of Eq. 22), computed once and stored as a float4;
+// Passes over the tiles that hold an interfacial (gated) cell, as listed by the phase-field kernel
+// of the previous step (or over every tile for the diagnostic read-back):
+//   k_nci_normals3 / k_nci_normals2  the normal n = grad(phi) / (|grad(phi)| + eps_n) of every gated
+//                  cell (Eq. 57, isotropic gradient of Eq. 22), computed once and stored as a float4;
+//                  in 3D also zero force at every gated cell and the normal ranges of each 4x4x4 brick;
+//   k_nci_prefilter (3D, sides multiples of 4) per listed tile, a lower bound of n(x).n(y) from the
+//                  brick ranges; only tiles where the facing gate can hold go on to the scan;
 //   k_nci_scan     per tile: phi and the gated normals of the tile + 3 halo staged in shared memory,
 //                  the gated cells of the tile compacted into a list, then one warp per gated cell
 //                  tests 32 window offsets per iteration in (|r|^2, canonical index) order and
