@@ -157,3 +157,7 @@ def test_partner_selection_brute_force(orc, dim, shape, seed):
     chi = part[:, 0] != orc.NO_PARTNER
     assert chi.sum() > 5
     assert np.array_equal(part.astype(np.int64), ref)
+    # partners beyond the inscribed sphere: the window is the full cube of (2w+1)^d - 1 positions
+    # (342 in 3D for w = 3, Sec. 2.3.2), not the ball |r| <= w
+    d2 = (part[chi].astype(np.int64) ** 2).sum(1)
+    assert d2.max() > cfg["w"] ** 2
