@@ -1,7 +1,7 @@
 """The lower bound behind the near-contact brick prefilter, checked against the oracle's pairing.
 
 For a 4x4x4 brick B with component ranges [lo, hi] of its gated normals, and [L, H] the ranges over
-the 27 bricks around it (which hold every cell y with |y - x| <= 3 of every x in B), the product is
+the 27 bricks around it (which hold every cell y with |y_a - x_a| <= 3 on each axis, for every x in B), the product is
 bilinear in each component, so n(x).n(y) >= sum_a min(lo_a L_a, lo_a H_a, hi_a L_a, hi_a H_a). A
 brick whose bound exceeds cos_opp + 1e-5 can hold no cell that meets the facing gate of Eq. 62. This
 test recomputes the bound in FP64 from the oracle's isotropic gradient (Eq. 22 normals, Eq. 57) on
