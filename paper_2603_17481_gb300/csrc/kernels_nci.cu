@@ -239,9 +239,10 @@ k_nci_normals3(const KParams P, const int32_t *__restrict__ phi, float4 *__restr
 
 // One 128-thread block per listed tile (3D). The tile's sixteen bricks are tested against the
 // union of the normal ranges of their 27 neighbouring bricks, a 10x4x3 box of bricks; a brick of a
-// tile that is not listed holds no gated cell and counts as empty. Every window offset of the
-// scan (every component |r_a| <= 3) stays inside those 27 bricks, so for a cell x of a brick with ranges [lo, hi]
-// and every gated y in its window, n(x).n(y) >= sum_a min(lo_a L_a, lo_a H_a, hi_a L_a, hi_a H_a),
+// tile that is not listed holds no gated cell and counts as empty. Every window offset of the scan
+// (each component |r_a| <= 3) stays inside those 27 bricks, so for a cell x of a brick with ranges
+// [lo, hi] and every gated y in its window,
+//   n(x).n(y) >= sum_a min(lo_a L_a, lo_a H_a, hi_a L_a, hi_a H_a),
 // [L, H] being the union (the product is bilinear, so its minimum over the two boxes is at a
 // corner). Where that bound exceeds cos_opp + 1e-5 for all sixteen bricks, no cell of the tile
 // can meet the facing gate (Eq. 62) and the tile keeps the zero force written by the normals
