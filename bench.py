@@ -190,7 +190,7 @@ def make_workload(Q=19):
     return cfg, phi, u
 
 
-def cpu_oracle_run(cfg, phi, u, budget_s, max_steps=5, min_steps=1):
+def cpu_oracle_run(cfg, phi, u, budget_s, max_steps=20, min_steps=1):
     """Times the FP64 oracle (as it stands) on the full grid for a bounded number of steps."""
     import oracle
     P = oracle.make_params(cfg)
