@@ -164,10 +164,12 @@ def whole_job_mlups(world, cells_per_rank, steps, ms_local, device=None):
     return world * cells_per_rank * steps / (ms_max * 1e-3) / 1e6, ms_max
 
 
-# The early horizon at which the store variants' phi is compared point by point: the droplets have
-# not met yet. After contact the flow is chaotic (a 2^-30 change of phi in one cell grows to
-# max|dphi| ~ 0.2 by step 2000 in FP32), so later comparisons use the droplet centroids.
+# Fixed horizons of the store-variant comparison, independent of --steps/--warmup (each on fresh
+# contexts): phi is compared point by point at EARLY, before the droplets meet; after contact the
+# flow is chaotic (a 2^-30 change of phi in one cell grows to max|dphi| ~ 0.2 by step 2000 in
+# FP32), so the LATE checkpoint compares the droplet centroids.
 EARLY = 200
+LATE = 1000
 
 
 def centroids(cfg, phi):
@@ -191,7 +193,8 @@ def make_workload(Q=19):
 
 
 def cpu_oracle_run(cfg, phi, u, budget_s, max_steps=20, min_steps=1):
-    """Times the FP64 oracle (as it stands) on the full grid for a bounded number of steps."""
+    """Times the FP64 oracle (as it stands) on the full grid for a bounded number of steps; also
+    returns its phi and velocity after those steps."""
     import oracle
     P = oracle.make_params(cfg)
     f = oracle.init(P, phi, u)
@@ -203,7 +206,22 @@ def cpu_oracle_run(cfg, phi, u, budget_s, max_steps=20, min_steps=1):
         f, ph, _ = oracle.step(P, f, ph, 1)
         t_total += time.perf_counter() - t0
         steps += 1
-    return N * steps / t_total / 1e6, steps, t_total
+    _, u_o = oracle.moments(P, f, ph)
+    return N * steps / t_total / 1e6, steps, t_total, ph, u_o
+
+
+def run_plan(args, world, rank):
+    """What one default run does, as plain numbers: every step count is non-negative whatever
+    --steps and --warmup are (the store variants use their own fixed horizons)."""
+    variants = bool(args.variants and args.store == "f32" and world == 1)
+    return {
+        "warmup": max(args.warmup, 0), "timed": max(args.steps, 0),
+        "split_steps": max(min(args.steps, 500), 1),
+        "e2e_steps": max(args.steps, 1) if not args.no_e2e else 0,
+        "variant_stores": ("f16", "bf16") if variants else (),
+        "variant_timed": max(args.steps, 1), "early": EARLY, "late": LATE,
+        "cpu_baseline": rank == 0 and world == 1 and not args.no_cpu_baseline,
+    }
 
 
 def run_ours(args, world, rank, local):
@@ -213,6 +231,7 @@ def run_ours(args, world, rank, local):
     from paper_2603_17481_gb300 import binding as B
     from paper_2603_17481_gb300 import build as lbm_build
 
+    plan = run_plan(args, world, rank)
     torch.cuda.set_device(local)
     lbm_build.build()
     cfg, phi, u = make_workload(args.lattice)
@@ -224,7 +243,7 @@ def run_ours(args, world, rank, local):
     m0, _ = sim.mass()
 
     # warm-up
-    sim.step(args.warmup)
+    sim.step(plan["warmup"])
     sim.synchronize()
 
     # timed region: K steps, with events on the library stream around the hydrodynamic kernel only
@@ -238,7 +257,7 @@ def run_ours(args, world, rank, local):
     time.sleep(0.3)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(plan["timed"]):
         sim.step(1)
     ev1.record(stream)
     ev1.synchronize()
@@ -250,10 +269,7 @@ def run_ours(args, world, rank, local):
     ms_total = ev0.elapsed_time(ev1)
     mlups, ms_max = whole_job_mlups(world, N, args.steps, ms_total, device=f"cuda:{local}")
     m1, _ = sim.mass()
-    n32 = args.warmup + args.steps
-    want_variants = args.variants and args.store == "f32" and world == 1
-    ph32 = sim.read_fields(want=("phi",))[0] if want_variants else None  # phi after n32 steps
-    split_steps = min(args.steps, 500)
+    split_steps = plan["split_steps"]
     sim.profile(True)
     sim.step(split_steps)
     split = sim.profile_read()
@@ -274,13 +290,13 @@ def run_ours(args, world, rank, local):
     # end-to-end through the C ABI with pinned host buffers: H2D of the initial fields, one
     # lbm_step call per step, D2H of the final fields
     e2e = None
-    if not args.no_e2e:
+    if plan["e2e_steps"]:
         phi_h = torch.from_numpy(np.ascontiguousarray(phi)).pin_memory()
         u_h = torch.from_numpy(np.ascontiguousarray(u)).reshape(-1).pin_memory()
         out_phi = torch.empty(N, dtype=torch.float64).pin_memory()
         out_u = torch.empty(3 * N, dtype=torch.float64).pin_memory()
         out_ps = torch.empty(N, dtype=torch.float64).pin_memory()
-        ke = args.steps
+        ke = plan["e2e_steps"]
         barrier(world)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -295,21 +311,29 @@ def run_ours(args, world, rank, local):
         e2e = {"value": round(world * N * ke / dt / 1e6, 1), "unit": "MLUPS",
                "h2d_bytes_per_step": round(h2d / ke, 1), "d2h_bytes_per_step": round(d2h / ke, 1),
                "steps": ke, "what": "lbm_init_fields(pinned host) + steps x lbm_step(1) + lbm_read_fields(pinned host)"}
+    sim.close()
+
+    def fresh(store, steps):
+        """phi after `steps` steps of the workload from its initial state, in a new context."""
+        s = B.Lbm(cfg, store=store, stream=stream.cuda_stream)
+        s.init_fields(phi, u)
+        s.step(steps)
+        ph_s = s.read_fields(want=("phi",))[0]
+        s.close()
+        return ph_s
 
     variants = {}
-    if want_variants:
-        # FP32 reference at the early horizon (before the droplets meet)
-        ref = B.Lbm(cfg, store="f32", stream=stream.cuda_stream)
-        ref.init_fields(phi, u)
-        ref.step(EARLY)
-        ph32_early = ref.read_fields(want=("phi",))[0]
-        ref.close()
-        for st in ("f16", "bf16"):
+    if plan["variant_stores"]:
+        # FP32 references at the fixed horizons
+        ph32_early, ph32_late = fresh("f32", plan["early"]), fresh("f32", plan["late"])
+        c32 = centroids(cfg, ph32_late)
+        for st in plan["variant_stores"]:
             s2 = B.Lbm(cfg, store=st, stream=stream.cuda_stream)
             s2.init_fields(phi, u)
-            s2.step(args.warmup)
+            mv0, _ = s2.mass()
+            s2.step(plan["warmup"])
             s2.synchronize()
-            kv = max(args.steps // 2, 10)
+            kv = plan["variant_timed"]
             s2.profile_kinds(["hydro"])  # as in the FP32 timed region
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -318,37 +342,45 @@ def run_ours(args, world, rank, local):
             e1.record(stream)
             e1.synchronize()
             pr = s2.profile_read()
+            s2.profile(False)
+            mv1, _ = s2.mass()
+            s2.close()
             msv = e0.elapsed_time(e1)
             hm, hn = pr["hydro"]
             v_mlups = N * kv / (msv * 1e-3) / 1e6
-            # phi after the same number of steps as the FP32 run, compared with it
-            s2.init_fields(phi, u)
-            s2.step(EARLY)
-            d_early = np.abs(s2.read_fields(want=("phi",))[0] - ph32_early)
-            s2.step(n32 - EARLY)
-            ph2, _, _ = s2.read_fields(want=("phi",))
+            d_early = np.abs(fresh(st, plan["early"]) - ph32_early)
+            ph_late = fresh(st, plan["late"])
             variants[st] = {
-                "value": round(v_mlups, 1), "steps": kv,
-                "hydro_gbs": round(hydro_bytes_per_cell(Q, 2) * N / (hm / hn * 1e-3) / 1e9, 1),
+                "value": round(v_mlups, 1), "steps": kv, "vs_f32": round(v_mlups / mlups, 4),
+                "hydro_gbs": round(hydro_bytes_per_cell(Q, 2) * N / (hm / max(hn, 1) * 1e-3) / 1e9, 1),
+                "hydro_ms": round(hm / max(hn, 1), 5),
                 "step_roofline_frac": round(v_mlups * 1e6 * step_bytes_per_cell(Q, 2) / (peak * 1e9), 4),
                 "phi_diff_vs_f32": {
-                    f"after_{EARLY}_steps": {"max": float(d_early.max()),
-                                             "q999": float(np.quantile(d_early, 0.999))},
-                    f"after_{n32}_steps": {"max": float(np.max(np.abs(ph2 - ph32))),
-                                           "centroid_max_cells": max(abs(a - b) for a, b in
-                                                                     zip(centroids(cfg, ph2), centroids(cfg, ph32)))}},
-                "phi_mass_drift": abs(s2.mass()[0] - m0) / abs(m0),
+                    f"after_{plan['early']}_steps": {"max": float(d_early.max()),
+                                                     "q999": float(np.quantile(d_early, 0.999))},
+                    f"after_{plan['late']}_steps": {
+                        "max": float(np.max(np.abs(ph_late - ph32_late))),
+                        "centroid_max_cells": max(abs(a - b) for a, b in zip(centroids(cfg, ph_late), c32))}},
+                "phi_mass_drift": abs(mv1 - mv0) / abs(mv0),
             }
-            s2.close()
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, steps, tt = cpu_oracle_run(cfg, phi, u, budget_s=args.cpu_budget)
+    cpu, vs_oracle = None, None
+    if plan["cpu_baseline"]:
+        v, steps, tt, ph_o, u_o = cpu_oracle_run(cfg, phi, u, budget_s=args.cpu_budget)
         cpu = {"value": round(v, 4), "unit": "MLUPS", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{steps} FP64 oracle step(s) of the full 256x128x128 grid, {tt:.1f} s, "
-                         f"OpenMP over all host cores"}
+               "sample": f"{steps} FP64 oracle step(s) of the full {cfg['nx']}x{cfg['ny']}x{cfg['nz']} grid, "
+                         f"{tt:.1f} s, OpenMP over all host cores"}
+        # every store against the FP64 oracle after the same steps, on the full grid
+        vs_oracle = {"steps": steps}
+        for st in ("f32",) + tuple(plan["variant_stores"]):
+            s = B.Lbm(cfg, store=st, stream=stream.cuda_stream)
+            s.init_fields(phi, u)
+            s.step(steps)
+            ph_g, u_g, _ = s.read_fields(want=("phi", "u"))
+            s.close()
+            vs_oracle[st] = {"max_dphi": float(np.max(np.abs(ph_g - ph_o))),
+                             "max_du": float(np.max(np.abs(u_g - u_o)))}
 
-    sim.close()
     if rank != 0:
         return None
     line = {
@@ -375,6 +407,8 @@ def run_ours(args, world, rank, local):
         "cpu_baseline": cpu,
         "phi_mass_drift": abs(m1 - m0) / abs(m0),
     }
+    if vs_oracle:
+        line["vs_fp64_oracle"] = vs_oracle
     if variants:
         line["variants"] = variants
     return line
@@ -724,7 +758,7 @@ def run_reference(args, world, rank):
     }
 
 
-def main():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
@@ -750,7 +784,14 @@ def main():
     ap.add_argument("--swarm-count-at", type=int, nargs="*", default=[], help="swarm: also count bubbles at these steps")
     ap.add_argument("--swarm-gap", type=float, default=2.0, help="swarm: minimum initial surface gap in units of eps")
     ap.add_argument("--diag-every", type=int, default=20, help="selftune: steps between film statistics")
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
+    if args.steps < 1 or args.warmup < 0:
+        ap.error("--steps must be >= 1 and --warmup >= 0")
+    return args
+
+
+def main():
+    args = parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         line = run_reference(args, world, rank)

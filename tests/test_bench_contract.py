@@ -24,3 +24,42 @@ def test_reference_arm_prints_one_contract_line(orc):
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in d["config"] and "sample" in d["config"]
+
+
+def _bench():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    return m
+
+
+import pytest  # noqa: E402
+
+
+@pytest.mark.parametrize("argv", [["--gpus", "1", "--steps", "20", "--warmup", "5"], ["--steps", "1", "--warmup", "0"],
+                                  ["--steps", "3", "--warmup", "3"], [], ["--steps", "2000", "--warmup", "20"]])
+def test_repo_arm_plan_has_no_negative_step_count(argv):
+    """The repo arm's step counts for any --steps/--warmup (the driver runs --steps 20 --warmup 5):
+    every count is non-negative and the store variants keep their own fixed horizons."""
+    bm = _bench()
+    args = bm.parse_args(argv)
+    plan = bm.run_plan(args, world=1, rank=0)
+    for k, v in plan.items():
+        if isinstance(v, int) and not isinstance(v, bool):
+            assert v >= 0, (k, v)
+    assert plan["timed"] == args.steps and plan["warmup"] == args.warmup
+    assert plan["variant_stores"] == ("f16", "bf16")
+    assert plan["early"] == bm.EARLY and plan["late"] == bm.LATE and bm.EARLY < bm.LATE
+    assert plan["variant_timed"] >= 1 and plan["split_steps"] >= 1 and plan["e2e_steps"] >= 1
+    assert plan["cpu_baseline"] is True
+    # other ranks and multi-GPU runs skip the variants and the CPU baseline
+    p2 = bm.run_plan(args, world=2, rank=1)
+    assert p2["variant_stores"] == () and p2["cpu_baseline"] is False
+
+
+def test_repo_arm_rejects_bad_step_counts():
+    bm = _bench()
+    for argv in (["--steps", "0"], ["--warmup", "-1"]):
+        with pytest.raises(SystemExit):
+            bm.parse_args(argv)
