@@ -130,8 +130,11 @@ int lbm_mass(lbm_ctx *ctx, double *phi_mass, double *mom);
  * Limits and errors: at most 16,777,216 cells (one slot per 4096 cells), else LBM_ERR_ARG; the
  * context's device must be current, else LBM_ERR_ARG; the moment buffer must already exist, i.e.
  * lbm_mass or lbm_read_fields ran once on this context, else LBM_ERR_STATE (it is not allocated
- * here). The first call on a device looks the scratch address up (cudaGetSymbolAddress); make that
- * first call during set-up, before any stream capture. All calls on a device share the scratch:
+ * here). The scratch lives in the library's module, which the CUDA runtime loads lazily: lbm_create
+ * looks its address up (cudaGetSymbolAddress) once per device, which loads the module and takes
+ * the 160 KB there, while allocating is allowed, so that no later call needs to. Should that
+ * look-up fail there, the first lbm_mass_noalloc call on the device repeats it (and then may take
+ * the memory itself); make that first call during set-up, before any stream capture. All calls on a device share the scratch:
  * calls whose work overlaps on the GPU (e.g. two contexts on different streams) race, so serialise
  * them. Each call overwrites every slot it reads; nothing needs clearing between calls.
  * Synchronises the context stream. Either output pointer may be NULL. */
@@ -183,7 +186,10 @@ typedef struct lbm_batch lbm_batch;
 int lbm_batch_create(lbm_ctx *const *ctxs, int n, int nstreams, void *stream, lbm_batch **out);
 /* Advances every context by nsteps: one graph launch per two steps, and for an odd nsteps a last
  * plain step of each context, all on the batch's launch stream. Asynchronous like lbm_step:
- * synchronise the launch stream (or call lbm_batch_synchronize) before reading results. */
+ * synchronise the launch stream (or call lbm_batch_synchronize) before reading results. Two graphs
+ * are captured at creation, one per ping-pong parity of the buffers (an odd nsteps flips it); a
+ * launch uses the one that every context holds. LBM_ERR_STATE if the contexts hold neither together
+ * (one was re-initialised or stepped outside the batch): nothing is launched. */
 int lbm_batch_step(lbm_batch *b, int nsteps);
 /* Waits for the batch's launch stream. */
 int lbm_batch_synchronize(lbm_batch *b);

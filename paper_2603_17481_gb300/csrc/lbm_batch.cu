@@ -5,6 +5,10 @@
 // launch advances every case by two steps (two, because the population and phi buffers ping-pong
 // and return to the same parity). Small cases then fill the GPU together instead of one after the
 // other, and the per-kernel launch cost is paid once per graph.
+//
+// A graph bakes in the buffers of the parity it was captured from. An odd step count ends with one
+// plain step per context, which flips every context's parity, so a second graph is captured from
+// the flipped parity and each launch picks the graph whose parity the contexts hold.
 #include <vector>
 
 #include "ctx.h"
@@ -16,8 +20,9 @@ struct lbm_batch {
   cudaStream_t stream = nullptr;  // capture stream
   cudaStream_t launch = nullptr;  // graph launches go here (the caller's stream, else `stream`)
   cudaEvent_t fork = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph[2] = {nullptr, nullptr};     // [0]: parity at creation, [1]: flipped
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  std::vector<int> cur0, pcur0;                  // each context's (cur, pcur) at creation
 };
 
 namespace {
@@ -31,8 +36,10 @@ int from_cuda_b(cudaError_t e) {
 extern "C" void lbm_batch_destroy(lbm_batch *b) {
   if (!b) return;
   if (b->launch) cudaStreamSynchronize(b->launch);
-  if (b->exec) cudaGraphExecDestroy(b->exec);
-  if (b->graph) cudaGraphDestroy(b->graph);
+  for (int g = 0; g < 2; g++) {
+    if (b->exec[g]) cudaGraphExecDestroy(b->exec[g]);
+    if (b->graph[g]) cudaGraphDestroy(b->graph[g]);
+  }
   for (auto e : b->joins) cudaEventDestroy(e);
   for (auto s : b->branches) cudaStreamDestroy(s);
   if (b->fork) cudaEventDestroy(b->fork);
@@ -72,35 +79,46 @@ extern "C" int lbm_batch_create(lbm_ctx *const *ctxs, int n, int nstreams, void 
     lbm_batch_destroy(b);
     return from_cuda_b(e);
   }
-  // capture two steps of every context
-  e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
-  int rc = LBM_OK;
-  if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->stream);
-  for (size_t s = 0; s < b->branches.size() && e == cudaSuccess; s++) e = cudaStreamWaitEvent(b->branches[s], b->fork, 0);
-  for (int i = 0; i < n && e == cudaSuccess && rc == LBM_OK; i++) {
-    lbm_ctx *c = ctxs[i];
-    const cudaStream_t saved = c->stream;
-    const int cur = c->cur, pcur = c->pcur;
-    const long long steps = c->steps;
-    c->stream = b->branches[i % b->branches.size()];
-    rc = lbm_step(c, 2);
-    c->stream = saved;
-    c->cur = cur;  // two steps return both ping-pong pairs to the same parity
-    c->pcur = pcur;
-    c->steps = steps;
+  for (int i = 0; i < n; i++) {
+    b->cur0.push_back(ctxs[i]->cur);
+    b->pcur0.push_back(ctxs[i]->pcur);
   }
-  for (size_t s = 0; s < b->branches.size() && e == cudaSuccess; s++) {
-    e = cudaEventRecord(b->joins[s], b->branches[s]);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->joins[s], 0);
+  // capture two steps of every context, once from the current parity and once from the flipped one
+  for (int g = 0; g < 2 && e == cudaSuccess; g++) {
+    int rc = LBM_OK;
+    e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->stream);
+    for (size_t s = 0; s < b->branches.size() && e == cudaSuccess; s++) e = cudaStreamWaitEvent(b->branches[s], b->fork, 0);
+    for (int i = 0; i < n && e == cudaSuccess && rc == LBM_OK; i++) {
+      lbm_ctx *c = ctxs[i];
+      const cudaStream_t saved = c->stream;
+      const long long steps = c->steps;
+      c->stream = b->branches[i % b->branches.size()];
+      c->cur = b->cur0[i] ^ g;
+      c->pcur = b->pcur0[i] ^ g;
+      rc = lbm_step(c, 2);
+      c->stream = saved;
+      c->cur = b->cur0[i];  // capture runs nothing: the contexts keep their state
+      c->pcur = b->pcur0[i];
+      c->steps = steps;
+    }
+    for (size_t s = 0; s < b->branches.size() && e == cudaSuccess; s++) {
+      e = cudaEventRecord(b->joins[s], b->branches[s]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->joins[s], 0);
+    }
+    cudaGraph_t gr = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(b->stream, &gr);
+    if (e == cudaSuccess) e = ee;
+    b->graph[g] = gr;
+    if (e == cudaSuccess && rc == LBM_OK) e = cudaGraphInstantiate(&b->exec[g], b->graph[g], 0);
+    if (e != cudaSuccess || rc != LBM_OK) {
+      lbm_batch_destroy(b);
+      return rc != LBM_OK ? rc : from_cuda_b(e);
+    }
   }
-  cudaGraph_t g = nullptr;
-  const cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
-  if (e == cudaSuccess) e = ee;
-  b->graph = g;
-  if (e == cudaSuccess && rc == LBM_OK) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
-  if (e != cudaSuccess || rc != LBM_OK) {
+  if (e != cudaSuccess) {
     lbm_batch_destroy(b);
-    return rc != LBM_OK ? rc : from_cuda_b(e);
+    return from_cuda_b(e);
   }
   *out = b;
   return LBM_OK;
@@ -108,8 +126,17 @@ extern "C" int lbm_batch_create(lbm_ctx *const *ctxs, int n, int nstreams, void 
 
 extern "C" int lbm_batch_step(lbm_batch *b, int nsteps) {
   if (!b || nsteps < 0) return LBM_ERR_ARG;
+  // the graph whose buffers are the ones every context currently holds
+  int g = -1;
+  for (size_t i = 0; i < b->ctxs.size(); i++) {
+    const lbm_ctx *c = b->ctxs[i];
+    const int gi = (c->cur == b->cur0[i] && c->pcur == b->pcur0[i]) ? 0
+                 : (c->cur == (b->cur0[i] ^ 1) && c->pcur == (b->pcur0[i] ^ 1)) ? 1 : -1;
+    if (gi < 0 || (g >= 0 && gi != g)) return LBM_ERR_STATE;
+    g = gi;
+  }
   cudaError_t e = cudaSuccess;
-  for (int k = 0; k + 1 < nsteps && e == cudaSuccess; k += 2) e = cudaGraphLaunch(b->exec, b->launch);
+  for (int k = 0; k + 1 < nsteps && e == cudaSuccess; k += 2) e = cudaGraphLaunch(b->exec[g], b->launch);
   if (e != cudaSuccess) return from_cuda_b(e);
   for (lbm_ctx *c : b->ctxs) c->steps += nsteps - (nsteps & 1);
   if (nsteps & 1) {

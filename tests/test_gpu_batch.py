@@ -54,7 +54,9 @@ def test_batch_matches_per_case_steps(nstreams):
             s.init_fields(phi, u)
             lst.append(s)
     batch = B.LbmBatch(batched, nstreams=nstreams)
-    for n in (4, 3, 0, 1):  # even (graph only), odd (graph + one plain step), none, plain only
+    # even (graph only), odd (graph + one plain step), none, plain only, then an odd count followed
+    # by an even one, so that the graph of the flipped buffer parity runs
+    for n in (4, 3, 0, 1, 3, 2, 1, 4):
         batch.step(n)
         for s in single:
             s.step(n)
@@ -89,6 +91,28 @@ def test_batch_case_against_oracle():
     phg, ug, _ = sims[0].read_fields()
     assert np.max(np.abs(phg - pho)) <= 1e-5
     assert np.max(np.abs(ug - uo)) <= 1e-6
+    batch.close()
+    for s in sims:
+        s.close()
+
+
+def test_batch_refuses_contexts_reinitialised_out_of_step():
+    """A context re-initialised outside the batch no longer holds either captured buffer parity
+    together with the others: the batch refuses to launch rather than step stale buffers."""
+    cfgs = [W.collision_sweep(1, seed=s, grids=(L,))[0] for s, L in ((11, 24), (12, 20))]
+    sims = []
+    for cfg in cfgs:
+        phi, u = W.sweep_case_fields(cfg)
+        s = B.Lbm(cfg)
+        s.init_fields(phi, u)
+        sims.append(s)
+    batch = B.LbmBatch(sims, nstreams=2)
+    batch.step(1)  # both contexts now hold the flipped parity
+    phi, u = W.sweep_case_fields(cfgs[0])
+    sims[0].init_fields(phi, u)  # back to the creation parity, the other context is not
+    with pytest.raises(B.LbmError) as e:
+        batch.step(2)
+    assert e.value.code == B.LBM_ERR_STATE
     batch.close()
     for s in sims:
         s.close()
