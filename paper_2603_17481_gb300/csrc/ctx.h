@@ -31,6 +31,7 @@ struct lbm_ctx {
   int32_t *partner = nullptr;
   int *tiles[2] = {nullptr, nullptr};
   int *ntiles = nullptr;  // 2 counters, one per phi buffer
+  int *lflag = nullptr;   // per near-contact tile: listed by the running phase pass (3D)
   lbm::NciAux aux;        // near-contact prefilter buffers (3D grids with sides multiple of 4)
   int nci_blocks = 0;
   lbm::ReduceOut *red_part = nullptr, *red_out = nullptr;
@@ -55,4 +56,8 @@ struct lbm_ctx {
 inline const lbm::NciAux *nci_aux(const lbm_ctx *c) { return c->aux.bricks ? &c->aux : nullptr; }
 // Kernels of one near-contact pass over the listed tiles: normals, prefilter (where it applies), scan.
 inline int nci_list_kernels(const lbm_ctx *c) { return nci_aux(c) ? 3 : 2; }
+
+// Looks up (once per device, current device) the static scratch of lbm_mass_noalloc, which loads
+// its module; lbm_create calls it. Returns an lbm_status.
+int lbm_noalloc_prepare_device();
 

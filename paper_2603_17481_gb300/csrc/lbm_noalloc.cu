@@ -44,6 +44,15 @@ int scratch_for_current_device(ReduceOut **out) {
 
 }  // namespace
 
+// Called by lbm_create with the context's device current. With lazy module loading (the CUDA
+// default), the module holding the static scratch is loaded, and its memory taken, on the first
+// use of one of its symbols; looking the address up here makes that happen while the library is
+// still allowed to allocate, not in the first lbm_mass_noalloc call.
+int lbm_noalloc_prepare_device() {
+  ReduceOut *scratch = nullptr;
+  return scratch_for_current_device(&scratch);
+}
+
 extern "C" int lbm_mass_noalloc(lbm_ctx *c, double *phi_mass, double *mom) {
   if (!c) return LBM_ERR_ARG;
   const long long nblocks = (c->N + kCellsPerBlock - 1) / kCellsPerBlock;
@@ -61,7 +70,7 @@ extern "C" int lbm_mass_noalloc(lbm_ctx *c, double *phi_mass, double *mom) {
   cudaError_t e = cudaSuccess;
   if (c->P.nci_on)
     e = launch_nci(c->P.dim, c->K, c->T, c->phi[c->pcur], c->nrm, c->frep, nullptr, 0, c->tiles[c->pcur],
-                   c->ntiles + c->pcur, c->nci_blocks, c->stream, nci_aux(c));
+                   c->ntiles + c->pcur, c->nci_blocks, c->stream, nci_aux(c), c->lflag);
   if (e == cudaSuccess)
     e = launch_hydro(c->P.Q, c->P.store, kMoments, c->K, c->pop[c->cur], nullptr, c->phi[c->pcur], c->frep,
                      c->mom, c->mom + 3 * c->N, nullptr, c->stream);

@@ -41,6 +41,27 @@ def test_noalloc_matches_lbm_mass_on_two_calls_in_a_row():
     m, mom = sim.mass_noalloc()
     assert abs(m - m_ref) <= 1e-12 * abs(m_ref)
     assert np.max(np.abs(mom - mom_ref)) <= 1e-9
+    sim.close()
+
+
+def test_noalloc_takes_no_device_memory():
+    """After one warm-up call, further calls leave the free device memory unchanged."""
+    import torch
+    cfg = W.base_config(3, 40, 32, 24, 19, rho_g=0.1)
+    phi, u = W.droplet_fields(cfg, [(12.5, 15.5, 11.5), (27.5, 16.0, 11.5)], [5.0, 5.0],
+                              [(0.02, 0, 0), (-0.02, 0, 0)])
+    sim = B.Lbm(cfg)
+    sim.init_fields(W.to_q30_grid(phi), u)
+    sim.mass()
+    sim.mass_noalloc()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(5):
+        sim.step(1)
+        sim.mass_noalloc()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    sim.close()
 
 
 def test_noalloc_refuses_what_it_cannot_do_without_allocating():
