@@ -114,6 +114,35 @@ def droplets_head_on_3d(nx=256, ny=128, nz=128, R=24.0, Q=19):
     return cfg, phi, u
 
 
+def droplets_paper_impact(case="E1", L=512, D=80.0, gap=8.0, Q=19, ratio=1000.0, shape=None):
+    """The paper's droplet-impact set-ups of Sec. 3.1 as synthetic stress workloads: a periodic L^3
+    box (paper: 512^3), two droplets of diameter D (paper: D_lu = 80), density ratio 1000,
+    sigma = 0.02, moving along x with relative speed U from We = rho_l U^2 D / sigma.
+    E1: head-on, We = 4.60, B = 0, nu_l = 0.005, nu_g = 0.05.
+    E2: off-axis, We = 4.8, B = 0.32 (centre offset B D along y), nu_l = 0.0012, nu_g = 0.012.
+    The paper does not state the initial separation; the surfaces start `gap` cells apart. `shape`
+    (nx, ny, nz) replaces the cubic box for reduced cases."""
+    if case == "E1":
+        we, B, nu_l, nu_g = 4.60, 0.0, 0.005, 0.05
+    elif case == "E2":
+        we, B, nu_l, nu_g = 4.8, 0.32, 0.0012, 0.012
+    else:
+        raise ValueError(case)
+    sigma, rho_l = 0.02, 1.0
+    nx, ny, nz = shape if shape is not None else (L, L, L)
+    cfg = base_config(3, nx, ny, nz, Q, rho_l=rho_l, rho_g=rho_l / ratio, nu_l=nu_l, nu_g=nu_g, sigma=sigma,
+                      A_rep=sigma)
+    U = math.sqrt(we * sigma / (rho_l * D))
+    R = D / 2.0
+    cx, cy, cz = (nx - 1) / 2.0, (ny - 1) / 2.0, (nz - 1) / 2.0
+    sep = 2 * R + gap
+    off = B * D
+    centers = [(cx - sep / 2, cy - off / 2, cz), (cx + sep / 2, cy + off / 2, cz)]
+    phi, u = droplet_fields(cfg, centers, [R, R], [(U / 2, 0, 0), (-U / 2, 0, 0)])
+    cfg.update(case=case, We=we, B=B, U_rel=U, diameter=D)
+    return cfg, phi, u
+
+
 #: Grid edges of the batched collision sweep (cubic periodic boxes).
 SWEEP_GRIDS = (48, 64, 80, 96)
 

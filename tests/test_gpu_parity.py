@@ -81,6 +81,63 @@ def test_single_step_identical_input(dim, Q, shape, seed, store):
     assert np.round(phg * 2 ** 30).sum() == m0  # exact fixed-point conservation
 
 
+@pytest.mark.parametrize("dim,Q,shape,seed,store", CASES_1STEP[:3])
+def test_single_step_fp64_decisions(dim, Q, shape, seed, store):
+    """The oracle with every near-contact decision (gate, similarity, facing, tie-break) taken in
+    FP64 on FP64 normals, against the kernels' binary32 decisions: partners identical except where
+    the FP64 decision margin is below 1e-5; then one step of populations and phi."""
+    cfg = W.base_config(dim, *shape, Q, rho_g=0.1, decide_f32=0)
+    P, phi, u, f = _random_state(cfg, seed)
+    assert P.decide_f32 == 0
+    sim = B.Lbm(cfg, store=store)
+    sim.set_state(f, phi)
+    nchi, _ = _compare_nci(sim, P, phi)
+    assert nchi > 0
+    part_g, _ = sim.read_nci()
+    part_o, _, _ = O.nci(P, phi)
+    diff = np.any(part_g != part_o, axis=1)
+    print(f"[parity] FP64 decisions: {int(diff.sum())} of {nchi} near-contact cells decided differently")
+    # a decision taken differently (only where its margin is below 1e-5, checked above) changes the
+    # force at its cell; one step carries that to the cell's lattice neighbours (streaming, and the
+    # face velocities of the phase update), which are left out of the comparison
+    reach = _dilate(diff, cfg)
+    sim.step(1)
+    fg, phg = sim.get_state()
+    fo, pho, _ = O.step(P, f, phi, 1)
+    assert np.max(np.abs(fg - fo)[:, ~reach]) < 1e-6
+    assert np.max(np.abs(phg - pho)[~reach]) < 1e-7
+
+
+def _dilate(mask, cfg):
+    """mask grown by one cell in every direction (3x3x3, 3x3 in 2D), periodic."""
+    g = mask.reshape(cfg["nz"], cfg["ny"], cfg["nx"])
+    out = g.copy()
+    zs = (-1, 0, 1) if cfg["dim"] == 3 else (0,)
+    for dz in zs:
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                out |= np.roll(g, (dz, dy, dx), axis=(0, 1, 2))
+    return out.ravel()
+
+
+@pytest.mark.parametrize("which", ["C1", "C2"])
+def test_trajectories_fp64_decisions_200_steps(which):
+    """The 2D head-on (C1) and 3D off-centre (C2) collisions against the oracle with FP64 near-contact
+    decisions: max|dphi| <= 1e-5 and max|du| <= 1e-6 after 200 steps."""
+    cfg, phi, u = W.droplets_head_on_2d() if which == "C1" else W.droplets_offcentre_3d()
+    cfg["decide_f32"] = 0
+    phi = W.to_q30_grid(phi)
+    P = O.make_params(cfg)
+    f = O.init(P, phi, u)
+    fo, pho, _ = O.step(P, f, phi, 200)
+    _, uo = O.moments(P, fo, pho)
+    sim = B.Lbm(cfg)
+    sim.init_fields(phi, u)
+    sim.step(200)
+    phg, ug, _ = sim.read_fields()
+    _check_traj(phg, pho, ug, uo)
+
+
 def test_head_on_2d_128x64_200_steps():
     """2D head-on collision (128x64 D2Q9), 200 steps: max|dphi| <= 1e-5, max|du| <= 1e-6."""
     cfg, phi, u = W.droplets_head_on_2d()
@@ -98,6 +155,7 @@ def test_head_on_2d_128x64_200_steps():
 
 def _check_traj(phg, pho, ug, uo, tphi=1e-5, tu=1e-6):
     dphi, du = float(np.max(np.abs(phg - pho))), float(np.max(np.abs(ug - uo)))
+    print(f"[parity] max|dphi|={dphi:.3e} max|du|={du:.3e}")
     assert dphi <= tphi and du <= tu, f"max|dphi|={dphi:.3e} (tol {tphi}), max|du|={du:.3e} (tol {tu})"
 
 
@@ -114,10 +172,20 @@ def test_head_on_2d_128x64_contact_400_steps():
     sim.init_fields(phi, u)
     sim.step(400)
     phg, ug, _ = sim.read_fields()
-    part_g, _ = sim.read_nci()
-    part_o, _, _ = O.nci(P, pho)
-    assert (part_o[:, 0] != O.NO_PARTNER).sum() > 0
     _check_traj(phg, pho, ug, uo)
+    # near-contact decisions on the GPU's own phi^400, same input on both sides: identical partners
+    # except where the oracle's decision margin is below 1e-5, forces within 2e-5 of their maximum
+    nchi, _ = _compare_nci(sim, P, phg)
+    assert nchi > 0
+    # and along the two trajectories: the GPU's partners on its phi against the oracle's on its own
+    # phi (they differ by <= 1e-5); a decision may differ only where the oracle's margin is below 1e-3
+    part_g, _ = sim.read_nci()
+    part_o, _, marg_o = O.nci(P, pho)
+    chi_o = part_o[:, 0] != O.NO_PARTNER
+    assert chi_o.sum() > 0
+    diff = np.any(part_g != part_o, axis=1)
+    assert np.all(marg_o[diff] < 1e-3), f"{diff.sum()} trajectory partner mismatches at robust cells"
+    assert diff.sum() <= 0.02 * chi_o.sum()
 
 
 def test_offcentre_3d_128x64x64_200_steps():
@@ -155,7 +223,7 @@ def test_d3q27_collision_200_steps():
     _check_traj(phg, pho, ug, uo)
 
 
-@pytest.mark.parametrize("store,tol", [("f16", 1e-3), ("bf16", 1e-2)])
+@pytest.mark.parametrize("store,tol", [("f16", 1e-3), ("bf16", 1e-3)])
 def test_half_precision_store_phi_error_and_mass(store, tol):
     """Populations stored as FP16/BF16 (f/w_i) with FP32 arithmetic, ratio-100 collision
     (128x64x64, R = 12), 200 steps: phi error against the FP64 oracle below tol, phi mass exact."""
@@ -249,27 +317,94 @@ def test_full_size_single_step_256x128x128():
     assert np.max(np.abs(phg - pho)) < 1e-7
 
 
-@pytest.mark.slow
+def _half_box_centroids(cfg, ph):
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    g = np.asarray(ph).reshape(nz, ny, nx)
+    out = []
+    for sl in (slice(0, nx // 2), slice(nx // 2, nx)):
+        m = g[:, :, sl]
+        zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx)[sl], indexing="ij")
+        out.append([(m * xx).sum() / m.sum(), (m * yy).sum() / m.sum(), (m * zz).sum() / m.sum()])
+    return np.array(out)
+
+
 def test_offcentre_3d_centroids_after_2000_steps():
-    """Droplet centroids (phi-weighted, per half-domain in x) within 0.05 cells after 2000 steps."""
+    """Droplet centroids (phi-weighted, per half-box in x) within 0.05 cells of the FP64 oracle's at
+    every stored checkpoint up to 2000 steps. The oracle's centroids are stored in
+    tests/golden/offcentre_3d_centroids.txt, written by make_offcentre_centroids.py beside it."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "offcentre_3d_centroids.txt")
+    rows = np.loadtxt(path, comments="#")
     cfg, phi, u = W.droplets_offcentre_3d()
+    phi = W.to_q30_grid(phi)
+    sim = B.Lbm(cfg)
+    sim.init_fields(phi, u)
+    done = 0
+    for row in rows:
+        step = int(row[0])
+        sim.step(step - done)
+        done = step
+        phg, _, _ = sim.read_fields(want=("phi",))
+        err = np.max(np.abs(_half_box_centroids(cfg, phg) - row[1:].reshape(2, 3)))
+        assert err <= 0.05, f"step {step}: centroid error {err:.4f} cells"
+    assert done == 2000
+
+
+@pytest.mark.parametrize("case", ["E1", "E2"])
+def test_paper_impacts_density_ratio_1000(case):
+    """The paper's impact set-ups (Sec. 3.1) at density ratio 1000, reduced to 128x64x64 with D = 20:
+    E1 head-on (We 4.6) and E2 off-axis (We 4.8, B = 0.32).
+    (a) the approach, 50 steps from the initial fields: max|dphi| <= 1e-5, max|du| <= 1e-6;
+    (b) at the oracle's own state after 100 steps (in contact, the repulsion active), identical input
+        on both sides: near-contact partners identical except where the oracle's decision margin is
+        below 1e-5, and one step of populations and phi within 1e-6 / 1e-7 outside the reach of a
+        decision taken differently.
+    Through contact the two trajectories are not compared point by point: the facing decisions of
+    Eqs. 61-65 are discontinuous, and in the mirror-symmetric head-on film a decision flipped by
+    binary32 rounding changes the force by O(A_rep) at that cell (measured: E1 departs to 1e-3 by
+    step 125 with the repulsion on, and stays at 1e-6 with it off)."""
+    cfg, phi, u = W.droplets_paper_impact(case, D=20.0, shape=(128, 64, 64))
     phi = W.to_q30_grid(phi)
     P = O.make_params(cfg)
     f = O.init(P, phi, u)
-    fo, pho, _ = O.step(P, f, phi, 2000)
+    f50, ph50, _ = O.step(P, f, phi, 50)
+    _, u50 = O.moments(P, f50, ph50)
     sim = B.Lbm(cfg)
     sim.init_fields(phi, u)
-    sim.step(2000)
-    phg, _, _ = sim.read_fields(want=("phi",))
+    sim.step(50)
+    phg, ug, _ = sim.read_fields()
+    _check_traj(phg, ph50, ug, u50)
+    f100, ph100, _ = O.step(P, f50, ph50, 50)
+    assert np.all(np.isfinite(f100)) and np.all(np.isfinite(ph100))
+    sim.set_state(f100, ph100)
+    nchi, _ = _compare_nci(sim, P, ph100)
+    assert nchi > 0, "the repulsion is not active at step 100"
+    part_g, _ = sim.read_nci()
+    part_o, _, _ = O.nci(P, ph100)
+    reach = _dilate(np.any(part_g != part_o, axis=1), cfg)
+    sim.step(1)
+    fg, phg = sim.get_state()
+    fo, pho, _ = O.step(P, f100, ph100, 1)
+    assert np.max(np.abs(fg - fo)[:, ~reach]) < 1e-6
+    assert np.max(np.abs(phg - pho)[~reach]) < 1e-7
+    sim.close()
 
-    def centroids(ph):
-        nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
-        g = ph.reshape(nz, ny, nx)
-        out = []
-        for sl in (slice(0, nx // 2), slice(nx // 2, nx)):
-            m = g[:, :, sl]
-            zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx)[sl], indexing="ij")
-            out.append([(m * xx).sum() / m.sum(), (m * yy).sum() / m.sum(), (m * zz).sum() / m.sum()])
-        return np.array(out)
 
-    assert np.max(np.abs(centroids(phg) - centroids(pho))) <= 0.05
+@pytest.mark.parametrize("case", ["E1", "E2"])
+def test_paper_impacts_density_ratio_1000_stable(case):
+    """The same reduced E1/E2 set-ups at density ratio 1000 on the GPU alone for 1500 steps, through
+    approach, contact and rebound: the periodic FP64 check finds no NaN/Inf, phi mass is exact, and
+    both droplets keep their liquid cores (phi > 1/2 somewhere in each half of the box)."""
+    cfg, phi, u = W.droplets_paper_impact(case, D=20.0, shape=(128, 64, 64))
+    phi = W.to_q30_grid(phi)
+    sim = B.Lbm(cfg, mass_check_every=100, mass_tol=0.0)
+    sim.init_fields(phi, u)
+    m0, _ = sim.mass()
+    sim.step(1500)
+    m1, _ = sim.mass()
+    phg, ug, _ = sim.read_fields()
+    assert m1 == m0
+    assert np.all(np.isfinite(phg)) and np.all(np.isfinite(ug))
+    assert np.max(np.abs(ug)) < 0.2
+    g = phg.reshape(cfg["nz"], cfg["ny"], cfg["nx"])
+    assert g[:, :, :cfg["nx"] // 2].max() > 0.5 and g[:, :, cfg["nx"] // 2:].max() > 0.5
+    sim.close()
