@@ -18,7 +18,10 @@
 // fixed-point phi grid and applied with opposite signs on its two cells, so sum(phi) is exactly
 // conserved. The kernel also lists the tiles of the near-contact kernel (same tiling) that hold an
 // interfacial cell of phi^{n+1}, so the next near-contact pass visits only those.
+#include <cstdlib>
+
 #include "launch.h"
+#include "phase3_march.cuh"
 
 namespace lbm {
 
@@ -556,19 +559,28 @@ static cudaError_t launch_phase_dim(const KParams &P, const int32_t *phi, const 
 
 // Raises k_phase3's dynamic shared-memory limit once. Context creation calls this, so that the
 // launches themselves make no non-stream CUDA call (they may be captured into a graph).
-// It also records how many k_phase3 blocks the device holds at once (SMs x resident blocks).
+// It also records how many k_phase3 blocks the device holds at once (SMs x resident blocks), and
+// the same for the register-march kernel.
 static int g_phase3_slots = 0;
+static int g_march_slots = 0;
+#ifndef LBM_MARCH_ROWS
+#define LBM_MARCH_ROWS 4
+#endif
+constexpr int kMarchRows = LBM_MARCH_ROWS;  // rows in y per thread of k_phase3m (2 or 4)
 
 cudaError_t phase_prepare(int dim) {
   static bool attr = false;
   if (dim != 3 || attr) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(k_phase3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Phase3::smem);
-  int dev = 0, sms = 0, per = 0;
+  int dev = 0, sms = 0, per = 0, perm = 0;
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_phase3, Phase3::NT, Phase3::smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perm, k_phase3m<kMarchRows>, March3::NT, 0);
   if (e == cudaSuccess) {
     g_phase3_slots = sms * (per > 0 ? per : 1);
+    g_march_slots = sms * (perm > 0 ? perm : 1);
     attr = true;
   }
   return e;
@@ -584,19 +596,35 @@ int phase3_zc(int nx, int ny, int nz) {
 }
 
 static cudaError_t launch_phase3(const KParams &P, const int32_t *phi, const float *u, int32_t *phi_out, int *tiles,
-                                 int *ntiles, cudaStream_t s) {
-  using G = Phase3;
+                                 int *ntiles, int *lflag, cudaStream_t s) {
   const cudaError_t e = phase_prepare(3);
   if (e != cudaSuccess) return e;
-  const int zc = phase3_zc(P.nx, P.ny, P.nz);
-  dim3 grid((P.nx + G::TX - 1) / G::TX, (P.ny + G::TY - 1) / G::TY, (P.nz + zc - 1) / zc);
-  return launch_pdl(k_phase3, grid, dim3(32, G::TY), G::smem, s, P, phi, u, phi_out, tiles, ntiles, zc);
+  static const bool old_kernel = [] {
+    const char *v = getenv("LBM_PHASE_KERNEL");
+    return v && v[0] == 'o';
+  }();
+  if (old_kernel) {
+    using G = Phase3;
+    const int zc = phase3_zc(P.nx, P.ny, P.nz);
+    dim3 grid((P.nx + G::TX - 1) / G::TX, (P.ny + G::TY - 1) / G::TY, (P.nz + zc - 1) / zc);
+    return launch_pdl(k_phase3, grid, dim3(32, G::TY), G::smem, s, P, phi, u, phi_out, tiles, ntiles, zc);
+  }
+  // one resident wave of warps sharing the (column, plane) units equally, at least MIN_RUN planes each
+  constexpr int M = kMarchRows;
+  const int ncx = (P.nx + March3::OUT - 1) / March3::OUT, ncy = (P.ny + M - 1) / M;
+  const long long units = (long long)ncx * ncy * P.nz;
+  const long long want = (units + March3::MIN_RUN - 1) / March3::MIN_RUN;
+  long long blocks = (want + March3::WARPS - 1) / March3::WARPS;
+  if (blocks > g_march_slots) blocks = g_march_slots;
+  if (blocks < 1) blocks = 1;
+  return launch_pdl(k_phase3m<M>, dim3((unsigned)blocks), dim3(March3::NT), 0, s, P, phi, u, phi_out, tiles, ntiles,
+                    lflag, ncx, units);
 }
 
 cudaError_t launch_phase(int dim, const KParams &P, const int32_t *phi, const float *u, int32_t *phi_out,
-                         int *tiles, int *ntiles, cudaStream_t s) {
+                         int *tiles, int *ntiles, int *lflag, cudaStream_t s) {
   return dim == 2 ? launch_phase_dim<2>(P, phi, u, phi_out, tiles, ntiles, s)
-                  : launch_phase3(P, phi, u, phi_out, tiles, ntiles, s);
+                  : launch_phase3(P, phi, u, phi_out, tiles, ntiles, lflag, s);
 }
 
 // Lists the tiles holding an interfacial cell of phi (used after the state is set from the host).

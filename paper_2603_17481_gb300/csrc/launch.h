@@ -50,9 +50,10 @@ size_t nci_brick_count(const KParams &P);
 // otherwise only the ntiles listed tiles, walked by list_blocks resident blocks. With aux (listed
 // tiles only), the normals pass also writes zero force at every gated cell and the brick ranges,
 // a prefilter keeps the tiles whose bricks may face another interface, and only those are scanned.
+// lflag (3D, listed tiles): the phase kernel's marks of the listed tiles, cleared here.
 cudaError_t launch_nci(int dim, const KParams &P, const NciTable &T, const int32_t *phi, float4 *nrm, float4 *frep,
                        int32_t *partner, int debug, const int *tiles, const int *ntiles, int list_blocks,
-                       cudaStream_t s, const NciAux *aux = nullptr);
+                       cudaStream_t s, const NciAux *aux = nullptr, int *lflag = nullptr);
 int nci_list_blocks(int dim);
 cudaError_t phase_prepare(int dim);
 
@@ -63,8 +64,10 @@ cudaError_t launch_hydro(int Q, int store, int mode, const KParams &P, const voi
                          cudaStream_t s);
 
 // Also appends to tiles/ntiles (if not null) the tiles of phi_out that hold an interfacial cell.
+// lflag (one int per near-contact tile, all zero on entry) marks the tiles already appended in 3D;
+// the near-contact normals pass that consumes the list clears the marks of its tiles.
 cudaError_t launch_phase(int dim, const KParams &P, const int32_t *phi, const float *u, int32_t *phi_out,
-                         int *tiles, int *ntiles, cudaStream_t s);
+                         int *tiles, int *ntiles, int *lflag, cudaStream_t s);
 cudaError_t launch_gate_tiles(int dim, const KParams &P, const int32_t *phi, int *tiles, int *ntiles, cudaStream_t s);
 int tile_count(int dim, const KParams &P);
 

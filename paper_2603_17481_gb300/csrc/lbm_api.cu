@@ -10,6 +10,7 @@
 //   mom      4*N float    u and p* of lbm_read_fields / lbm_mass (allocated on first use)
 //   stage    k*N double   FP64 staging of host I/O (allocated on first use, grown as needed)
 //   tiles[2] int          near-contact tiles holding an interfacial cell of phi[k] (+ 2 counts)
+//   lflag    int          per near-contact tile: already listed by the current phase pass
 //   red      reduction partials and result
 #include <algorithm>
 #include <climits>
@@ -161,6 +162,8 @@ int sync(lbm_ctx *c) { return from_cuda(cudaStreamSynchronize(c->stream)); }
 int finish_init(lbm_ctx *c) {
   int rc = from_cuda(cudaMemsetAsync(c->ntiles, 0, 2 * sizeof(int), c->stream));
   if (rc) return rc;
+  rc = from_cuda(cudaMemsetAsync(c->lflag, 0, sizeof(int) * tile_count(c->P.dim, c->K), c->stream));
+  if (rc) return rc;
   rc = from_cuda(launch_gate_tiles(c->P.dim, c->K, c->phi[c->pcur], c->tiles[c->pcur], c->ntiles + c->pcur, c->stream));
   if (rc) return rc;
   rc = from_cuda(launch_reduce(c->K, c->phi[c->pcur], c->u, c->red_part, c->red_out, c->stream));
@@ -184,7 +187,7 @@ int run_moments(lbm_ctx *c) {
   if (c->P.nci_on) {
     rc = from_cuda(timed(c, LBM_K_NCI, [&] {
       return launch_nci(d, c->K, c->T, c->phi[c->pcur], c->nrm, c->frep, nullptr, 0, c->tiles[c->pcur],
-                        c->ntiles + c->pcur, c->nci_blocks, c->stream, nci_aux(c));
+                        c->ntiles + c->pcur, c->nci_blocks, c->stream, nci_aux(c), c->lflag);
     }, nci_list_kernels(c)));
     if (rc) return rc;
   }
@@ -233,6 +236,8 @@ int lbm_create(const lbm_params *p, lbm_ctx **out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->tiles[1], sizeof(int) * ntile);
   if (e == cudaSuccess) e = cudaMalloc(&c->ntiles, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->ntiles, 0, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->lflag, sizeof(int) * ntile);
+  if (e == cudaSuccess) e = cudaMemset(c->lflag, 0, sizeof(int) * ntile);
   if (e == cudaSuccess && p->nci_on && nci_aux_applies(p->dim, c->K)) {
     e = cudaMalloc(&c->aux.bricks, sizeof(uint4) * nci_brick_count(c->K));
     if (e == cudaSuccess) e = cudaMalloc(&c->aux.flags, (size_t)ntile);
@@ -246,6 +251,9 @@ int lbm_create(const lbm_params *p, lbm_ctx **out) {
     if (c->nci_blocks <= 0) e = cudaErrorInvalidConfiguration;
   }
   if (e == cudaSuccess) e = phase_prepare(p->dim);
+  // the static scratch of lbm_mass_noalloc is taken here, once per device, while allocating is
+  // allowed; a failure is not the context's (lbm_mass_noalloc repeats the look-up and reports it)
+  if (e == cudaSuccess) (void)lbm_noalloc_prepare_device();
   if (e == cudaSuccess) e = cudaMalloc(&c->red_part, sizeof(ReduceOut) * kReduceBlocks);
   if (e == cudaSuccess) e = cudaMalloc(&c->red_out, sizeof(ReduceOut));
   if (e == cudaSuccess) e = cudaMemset(c->u, 0, sizeof(float) * 3 * c->N);
@@ -274,7 +282,7 @@ void lbm_destroy(lbm_ctx *c) {
   cudaFree(c->partner); cudaFree(c->red_part); cudaFree(c->red_out);
   cudaFree(c->diag_part); cudaFree(c->diag_out);
   cudaFree(c->curv_hist); cudaFree(c->curv_part);
-  cudaFree(c->tiles[0]); cudaFree(c->tiles[1]); cudaFree(c->ntiles);
+  cudaFree(c->tiles[0]); cudaFree(c->tiles[1]); cudaFree(c->ntiles); cudaFree(c->lflag);
   cudaFree(c->aux.bricks); cudaFree(c->aux.flags); cudaFree(c->aux.scan_tiles); cudaFree(c->aux.nscan);
   delete c;
 }
@@ -357,7 +365,7 @@ int lbm_step(lbm_ctx *c, int n) {
     if (nci) {
       rc = from_cuda(timed(c, LBM_K_NCI, [&] {
         return launch_nci(d, c->K, c->T, c->phi[c->pcur], c->nrm, c->frep, nullptr, 0, c->tiles[c->pcur],
-                          c->ntiles + c->pcur, c->nci_blocks, c->stream, nci_aux(c));
+                          c->ntiles + c->pcur, c->nci_blocks, c->stream, nci_aux(c), c->lflag);
       }, nci_list_kernels(c)));
       if (rc) return rc;
     }
@@ -368,7 +376,7 @@ int lbm_step(lbm_ctx *c, int n) {
     if (rc) return rc;
     rc = from_cuda(timed(c, LBM_K_PHASE, [&] {
       return launch_phase(d, c->K, c->phi[c->pcur], c->u, c->phi[pn], nci ? c->tiles[pn] : nullptr,
-                          nci ? c->ntiles + pn : nullptr, c->stream);
+                          nci ? c->ntiles + pn : nullptr, c->lflag, c->stream);
     }));
     if (rc) return rc;
     c->cur = nxt;
@@ -480,7 +488,7 @@ int lbm_nci_diagnostics(lbm_ctx *c, double *out) {
   // the near-contact pass over the tiles listed for the current phi (the list stays for the next step)
   int rc = from_cuda(timed(c, LBM_K_NCI, [&] {
     return launch_nci(c->P.dim, c->K, c->T, c->phi[c->pcur], c->nrm, c->frep, nullptr, 0, c->tiles[c->pcur],
-                      c->ntiles + c->pcur, c->nci_blocks, c->stream, nci_aux(c));
+                      c->ntiles + c->pcur, c->nci_blocks, c->stream, nci_aux(c), c->lflag);
   }, nci_list_kernels(c)));
   if (rc) return rc;
   rc = from_cuda(timed(c, LBM_K_REDUCE, [&] {

@@ -1,0 +1,242 @@
+// phase3_march.cuh -- the 3D phase-field update (Sec. 2.1.1, Eq. 28) as a register march.
+//
+// The transfers are those of kernels_phase.cu (same face-flux form, same separable (1, 4, 1)
+// smoothings of the D3Q27 weights, one rounding to 2^-30 per face), but organised so that a thread
+// keeps everything it needs in registers:
+//   - a warp owns 32 consecutive x columns and writes the middle 28 (lanes 2..29); every x
+//     neighbour (x +- 1, x + 2) is a warp shuffle, and the two columns of halo on each side are
+//     computed by the warp itself (12.5 % redundant lanes instead of shared-memory staging);
+//   - a thread owns M consecutive rows in y (it also holds the halo rows y - 2 .. y + M + 1 of phi
+//     and y - 1 .. y + M of the compressive vector a), so every y neighbour is a register;
+//   - the warp marches along z over a contiguous run of planes, keeping the few planes of phi, of
+//     a and of the transfers it still needs; every z neighbour is a register too.
+// There is no shared memory and no block barrier. Warps take equal shares of the (column, plane)
+// work units, so the grid is one resident wave. A face on the boundary between two warps' ranges is
+// computed by both from identical inputs with the same operations, so its rounded transfer is the
+// same on both sides and sum(phi) stays exact.
+//
+// With g = G / 72 the normal is n = G / (|G| + 72 eps_n) (the factor of the D3Q27 gradient folds
+// into eps_n), and with T = s_y s_z phi, Rz = s_z phi, the face transfers are
+//   x: u_f phi_up + (D / 36)(T(x) - T(x+1)) + (3 kappa / 216)(s_y s_z a_x (x) + s_y s_z a_x (x+1))
+//   y: u_f phi_up + (D / 6)(Rz(y) - Rz(y+1)) + (3 kappa / 216)(s_x s_z a_y (y) + s_x s_z a_y (y+1))
+//   z: u_f phi_up + D (phi(z) - phi(z+1)) + (3 kappa / 216)(s_x s_y a_z (z) + s_x s_y a_z (z+1))
+// and g = (s_y s_z d_x phi, s_x s_z d_y phi, s_x s_y d_z phi) / 72 with d the central difference.
+#pragma once
+
+#include "launch.h"
+
+namespace lbm {
+
+struct March3 {
+  static constexpr int OUT = 28;       // output columns per warp
+  static constexpr int WARPS = 4;      // warps per block
+  static constexpr int NT = 32 * WARPS;
+  static constexpr int MIN_RUN = 8;    // fewest planes per warp before the grid is shrunk
+};
+
+__device__ __forceinline__ float sh_up(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }      // x - 1
+__device__ __forceinline__ float sh_dn(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }    // x + 1
+__device__ __forceinline__ float sh_dn2(float v) { return __shfl_down_sync(0xffffffffu, v, 2); }   // x + 2
+__device__ __forceinline__ int sh_up_i(int v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ float m141(float a, float b, float c) { return fmaf(4.0f, b, a + c); }
+
+// minmod(a, b): the argument of smaller magnitude when both have the same sign, else 0.
+__device__ __forceinline__ float mm_f(float a, float b) {
+  return a * b > 0.0f ? copysignf(fminf(fabsf(a), fabsf(b)), a) : 0.0f;
+}
+// Upwind MUSCL state at the face between p and p + e from phi(p - e), phi(p), phi(p + e),
+// phi(p + 2e) (Eqs. 30-34): with (L, C, R) = (p - e, p, p + e) when u_f >= 0 and
+// (p + 2e, p + e, p) otherwise, C + minmod(C - L, R - C) / 2.
+__device__ __forceinline__ float upw(float uf, float vm, float v0, float v1, float vp) {
+  const bool pos = uf >= 0.0f;
+  const float L = pos ? vm : vp, C = pos ? v0 : v1, R = pos ? v1 : v0;
+  return fmaf(0.5f, mm_f(C - L, R - C), C);
+}
+
+// Resident blocks per SM the registers are sized for.
+#ifndef LBM_MARCH_MINB
+#define LBM_MARCH_MINB 3
+#endif
+
+template <int M>
+__global__ void __launch_bounds__(March3::NT, LBM_MARCH_MINB)
+k_phase3m(const KParams P, const int32_t *__restrict__ phi, const float *__restrict__ u,
+          int32_t *__restrict__ phi_out, int *__restrict__ tiles, int *__restrict__ ntiles, int *__restrict__ lflag,
+          const int ncx, const long long units) {
+  pdl_enter();
+  constexpr int NR = M + 4;  // phi rows -2 .. M+1 (index r + 2)
+  constexpr int NA = M + 2;  // rows -1 .. M (index r + 1)
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = (long long)gridDim.x * March3::WARPS;
+  const long long wid = (long long)blockIdx.x * March3::WARPS + (threadIdx.x >> 5);
+  long long ub = units * wid / nwarps;
+  const long long ue = units * (wid + 1) / nwarps;
+  const int nx = P.nx, ny = P.ny, nz = P.nz;
+  const int plane = nx * ny;
+  const float *__restrict__ ux = u;
+  const float *__restrict__ uy = u + P.N;
+  const float *__restrict__ uz = u + 2 * P.N;
+  const float D = P.Dlap * (1.0f / 6.0f), Dx = D * (1.0f / 36.0f), Dy = D * (1.0f / 6.0f);
+  const float k3s = P.kc * kCs2 * 3.0f * (1.0f / 216.0f);
+  const float e72 = 72.0f * P.eps_n;
+  const int gtx = (nx + 31) / 32, gty = (ny + 7) / 8;
+
+  while (ub < ue) {
+    const long long col = ub / nz;
+    const int z0 = (int)(ub - col * nz);
+    const int z1 = (int)min((long long)nz, (long long)z0 + (ue - ub));
+    ub += z1 - z0;
+    const int ix = (int)(col % ncx), iy = (int)(col / ncx);
+    const int xs = ix * March3::OUT, ys = iy * M;
+    const int x = wrapi(xs + lane - 2, nx);
+    const bool xout = lane >= 2 && lane < 2 + March3::OUT && xs + lane - 2 < nx;
+    int yo[NR];  // in-plane offsets of this thread's cells in rows -2 .. M+1
+#pragma unroll
+    for (int i = 0; i < NR; i++) yo[i] = wrapi(ys + i - 2, ny) * nx + x;
+    // near-contact tiles (32 x 8 x 4) touched by the output columns: x tiles tx0 and tx1
+    const int tx0 = xs / 32, tx1 = min(xs + March3::OUT - 1, nx - 1) / 32;
+    unsigned tflag = 0;  // bit 0: tile tx0, bit 1: tile tx1, for the current group of 4 planes
+
+    float F0[NR], F1[NR], F2[NR], Fm[M];  // phi of planes p-2, p-1, p, and p-3 (rows 0..M-1)
+    float RZk[NA];                        // s_z phi of plane p-2, rows -1..M
+    float HX0[NA], HX1[NA], HY0[NA], HY1[NA];  // a_x, a_y of planes p-3, p-2, rows -1..M
+    float ASk[M], UZk[M];                 // s_x s_y a_z and u_z of plane p-2
+    int TZk[M];                           // transfer of the z face below plane p-2
+#pragma unroll
+    for (int i = 0; i < NR; i++) { F0[i] = 0.f; F1[i] = 0.f; }
+#pragma unroll
+    for (int i = 0; i < NA; i++) { RZk[i] = 0.f; HX0[i] = HX1[i] = HY0[i] = HY1[i] = 0.f; }
+#pragma unroll
+    for (int r = 0; r < M; r++) { Fm[r] = 0.f; ASk[r] = 0.f; UZk[r] = 0.f; TZk[r] = 0; }
+
+    for (int p = z0 - 2; p <= z1 + 1; p++) {
+      const int pz = wrapi(p, nz) * plane;
+      // phi of plane p
+#pragma unroll
+      for (int i = 0; i < NR; i++) F2[i] = phi_of(__ldg(phi + pz + yo[i]));
+      float uzn[M], uxk[M], uyk[NA];
+      const int pz1 = wrapi(p - 1, nz) * plane, pz2 = wrapi(p - 2, nz) * plane;
+      if (p >= z0) {
+#pragma unroll
+        for (int r = 0; r < M; r++) uzn[r] = __ldg(uz + pz1 + yo[r + 2]);
+      }
+      if (p >= z0 + 2) {
+#pragma unroll
+        for (int r = 0; r < M; r++) uxk[r] = __ldg(ux + pz2 + yo[r + 2]);
+#pragma unroll
+        for (int i = 0; i < NA; i++) uyk[i] = __ldg(uy + pz2 + yo[i + 1]);
+      }
+      float RZ1[NR], ax[NA], ay[NA], ASn[M];
+      if (p >= z0) {
+        // a = phi (1 - phi) n at plane p - 1, rows -1..M
+#pragma unroll
+        for (int i = 0; i < NR; i++) RZ1[i] = m141(F0[i], F1[i], F2[i]);
+        float az[NA];
+#pragma unroll
+        for (int i = 0; i < NA; i++) {
+          const float syr = m141(RZ1[i], RZ1[i + 1], RZ1[i + 2]);
+          const float gx = sh_dn(syr) - sh_up(syr);
+          const float dy = RZ1[i + 2] - RZ1[i];
+          const float gy = m141(sh_up(dy), dy, sh_dn(dy));
+          const float syd = m141(F2[i] - F0[i], F2[i + 1] - F0[i + 1], F2[i + 2] - F0[i + 2]);
+          const float gz = m141(sh_up(syd), syd, sh_dn(syd));
+          const float ph = F1[i + 1];
+          const float gg = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+          const float gn = gg > 0.0f ? gg * rsqrtf(gg) : 0.0f;
+          const float sc = __fdividef(ph * (1.0f - ph), gn + e72);
+          ax[i] = gx * sc;
+          ay[i] = gy * sc;
+          az[i] = gz * sc;
+        }
+#pragma unroll
+        for (int r = 0; r < M; r++) {
+          const float sy = m141(az[r], az[r + 1], az[r + 2]);
+          ASn[r] = m141(sh_up(sy), sy, sh_dn(sy));
+        }
+      }
+      int TZn[M];
+      if (p >= z0 + 1) {
+        // z face between planes p-2 and p-1, rows 0..M-1
+#pragma unroll
+        for (int r = 0; r < M; r++) {
+          const float v0 = F0[r + 2], v1 = F1[r + 2];
+          const float uf = 0.5f * (UZk[r] + uzn[r]);
+          const float up = upw(uf, Fm[r], v0, v1, F2[r + 2]);
+          TZn[r] = __float2int_rn(kQ30 * fmaf(D, v0 - v1, fmaf(k3s, ASk[r] + ASn[r], uf * up)));
+        }
+      }
+      if (p >= z0 + 2) {
+        // output plane k = p - 2: x and y faces, then the update
+        const int k = p - 2;
+        int TX[M], TY[M + 1];
+#pragma unroll
+        for (int r = 0; r < M; r++) {
+          const float T = m141(RZk[r], RZk[r + 1], RZk[r + 2]);
+          const float AX = m141(m141(HX0[r], HX1[r], ax[r]), m141(HX0[r + 1], HX1[r + 1], ax[r + 1]),
+                                m141(HX0[r + 2], HX1[r + 2], ax[r + 2]));
+          const float v0 = F0[r + 2];
+          const float vm = sh_up(v0), v1 = sh_dn(v0), vp = sh_dn2(v0);
+          const float uf = 0.5f * (uxk[r] + sh_dn(uxk[r]));
+          const float up = upw(uf, vm, v0, v1, vp);
+          TX[r] = __float2int_rn(kQ30 * fmaf(Dx, T - sh_dn(T), fmaf(k3s, AX + sh_dn(AX), uf * up)));
+        }
+        float AY[NA];
+#pragma unroll
+        for (int i = 0; i < NA; i++) {
+          const float a = m141(HY0[i], HY1[i], ay[i]);
+          AY[i] = m141(sh_up(a), a, sh_dn(a));
+        }
+#pragma unroll
+        for (int j = 0; j < M + 1; j++) {  // face between rows j - 1 and j
+          const float uf = 0.5f * (uyk[j] + uyk[j + 1]);
+          const float up = upw(uf, F0[j], F0[j + 1], F0[j + 2], F0[j + 3]);
+          TY[j] = __float2int_rn(kQ30 * fmaf(Dy, RZk[j] - RZk[j + 1], fmaf(k3s, AY[j] + AY[j + 1], uf * up)));
+        }
+        const int kz = wrapi(k, nz) * plane;
+        bool g0 = false, g1 = false;
+#pragma unroll
+        for (int r = 0; r < M; r++) {
+          const int acc = sh_up_i(TX[r]) - TX[r] + TY[r] - TY[r + 1] + TZk[r] - TZn[r];
+          if (xout && ys + r < ny) {
+            const int32_t vn = __ldg(phi + kz + yo[r + 2]) + acc;
+            phi_out[kz + yo[r + 2]] = vn;
+            if (tiles && q_gate_value(vn) >= P.q_th) {
+              if ((xs + lane - 2) / 32 == tx0) g0 = true; else g1 = true;
+            }
+          }
+        }
+        if (tiles) {
+          tflag |= (__any_sync(0xffffffffu, g0) ? 1u : 0u) | (__any_sync(0xffffffffu, g1) ? 2u : 0u);
+          if ((k & 3) == 3 || k == z1 - 1) {
+            if (lane < 2 && ((tflag >> lane) & 1u)) {
+              const int tile = (lane ? tx1 : tx0) + gtx * ((ys >> 3) + gty * (k >> 2));
+              if (atomicExch(lflag + tile, 1) == 0) tiles[atomicAdd(ntiles, 1)] = tile;
+            }
+            tflag = 0;
+          }
+        }
+      }
+      // advance the histories by one plane
+      if (p >= z0 + 1) {
+#pragma unroll
+        for (int r = 0; r < M; r++) TZk[r] = TZn[r];
+      }
+      if (p >= z0) {
+#pragma unroll
+        for (int r = 0; r < M; r++) { ASk[r] = ASn[r]; UZk[r] = uzn[r]; }
+#pragma unroll
+        for (int i = 0; i < NA; i++) {
+          RZk[i] = RZ1[i + 1];
+          HX0[i] = HX1[i]; HX1[i] = ax[i];
+          HY0[i] = HY1[i]; HY1[i] = ay[i];
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < M; r++) Fm[r] = F0[r + 2];
+#pragma unroll
+      for (int i = 0; i < NR; i++) { F0[i] = F1[i]; F1[i] = F2[i]; }
+    }
+  }
+}
+
+}  // namespace lbm
