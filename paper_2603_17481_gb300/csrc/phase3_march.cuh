@@ -16,11 +16,12 @@
 // same on both sides and sum(phi) stays exact.
 //
 // With g = G / 72 the normal is n = G / (|G| + 72 eps_n) (the factor of the D3Q27 gradient folds
-// into eps_n), and with T = s_y s_z phi, Rz = s_z phi, the face transfers are
-//   x: u_f phi_up + (D / 36)(T(x) - T(x+1)) + (3 kappa / 216)(s_y s_z a_x (x) + s_y s_z a_x (x+1))
-//   y: u_f phi_up + (D / 6)(Rz(y) - Rz(y+1)) + (3 kappa / 216)(s_x s_z a_y (y) + s_x s_z a_y (y+1))
+// into eps_n), and the face transfers are
+//   x: u_f phi_up + (D / 36) s_y s_z (phi(x) - phi(x+1)) + (3 kappa / 216)(s_y s_z a_x (x) + s_y s_z a_x (x+1))
+//   y: u_f phi_up + (D / 6) s_z (phi(y) - phi(y+1)) + (3 kappa / 216)(s_x s_z a_y (y) + s_x s_z a_y (y+1))
 //   z: u_f phi_up + D (phi(z) - phi(z+1)) + (3 kappa / 216)(s_x s_y a_z (z) + s_x s_y a_z (z+1))
-// and g = (s_y s_z d_x phi, s_x s_z d_y phi, s_x s_y d_z phi) / 72 with d the central difference.
+// and G = (s_y s_z d_x phi, s_x s_z d_y phi, s_x s_y d_z phi) with d the central difference, built
+// from the one-sided differences phi(x) - phi(x+1) as d_x phi(x) = -(those at x and x - 1).
 #pragma once
 
 #include "launch.h"
@@ -34,28 +35,37 @@ struct March3 {
   static constexpr int MIN_RUN = 8;    // fewest planes per warp before the grid is shrunk
 };
 
-__device__ __forceinline__ float sh_up(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }      // x - 1
-__device__ __forceinline__ float sh_dn(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }    // x + 1
-__device__ __forceinline__ float sh_dn2(float v) { return __shfl_down_sync(0xffffffffu, v, 2); }   // x + 2
+__device__ __forceinline__ float sh_up(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }    // x - 1
+__device__ __forceinline__ float sh_dn(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }  // x + 1
 __device__ __forceinline__ int sh_up_i(int v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ int sh_dn_i(int v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ int sh_dn2_i(int v) { return __shfl_down_sync(0xffffffffu, v, 2); }
 __device__ __forceinline__ float m141(float a, float b, float c) { return fmaf(4.0f, b, a + c); }
+__device__ __forceinline__ float i2f(int32_t v) { return __int2float_rn(v); }
 
-// minmod(a, b): the argument of smaller magnitude when both have the same sign, else 0.
-__device__ __forceinline__ float mm_f(float a, float b) {
-  return a * b > 0.0f ? copysignf(fminf(fabsf(a), fabsf(b)), a) : 0.0f;
+// minmod of two exact fixed-point differences: the one of smaller magnitude when both have the
+// same sign, else 0.
+__device__ __forceinline__ int32_t mm_i(int32_t a, int32_t b) {
+  const int32_t lo = min(a, b), hi = max(a, b);
+  return lo > 0 ? lo : (hi < 0 ? hi : 0);
 }
-// Upwind MUSCL state at the face between p and p + e from phi(p - e), phi(p), phi(p + e),
-// phi(p + 2e) (Eqs. 30-34): with (L, C, R) = (p - e, p, p + e) when u_f >= 0 and
-// (p + 2e, p + e, p) otherwise, C + minmod(C - L, R - C) / 2.
-__device__ __forceinline__ float upw(float uf, float vm, float v0, float v1, float vp) {
+// Upwind MUSCL state at the face between p and p + e (Eqs. 30-34), in 2^-30 units, from the
+// fixed-point phi at p - e, p, p + e, p + 2e: with (L, C, R) = (p - e, p, p + e) when u_f >= 0
+// and (p + 2e, p + e, p) otherwise, C + minmod(C - L, R - C) / 2; the slopes are exact integers.
+__device__ __forceinline__ float upw_i(float uf, int32_t vm, int32_t v0, int32_t v1, int32_t vp) {
   const bool pos = uf >= 0.0f;
-  const float L = pos ? vm : vp, C = pos ? v0 : v1, R = pos ? v1 : v0;
-  return fmaf(0.5f, mm_f(C - L, R - C), C);
+  const int32_t L = pos ? vm : vp, C = pos ? v0 : v1, R = pos ? v1 : v0;
+  return fmaf(0.5f, i2f(mm_i(C - L, R - C)), i2f(C));
 }
 
+// One warp's march over a run of planes. Phi is kept as fixed-point integers; every difference
+// of phi (gradient, diffusion, MUSCL slopes) is taken exactly in integers before it is converted,
+// so stencils keep their precision where phi is close to 1 (a float copy of phi near 1 resolves
+// only 6e-8, which in the liquid interior, where |grad phi| is small but phi (1 - phi) is not,
+// steers the normal of the compressive term). Quantities in 2^-30 units carry the suffix _q.
 // Resident blocks per SM the registers are sized for.
 #ifndef LBM_MARCH_MINB
-#define LBM_MARCH_MINB 3
+#define LBM_MARCH_MINB 2
 #endif
 
 template <int M>
@@ -66,19 +76,22 @@ k_phase3m(const KParams P, const int32_t *__restrict__ phi, const float *__restr
   pdl_enter();
   constexpr int NR = M + 4;  // phi rows -2 .. M+1 (index r + 2)
   constexpr int NA = M + 2;  // rows -1 .. M (index r + 1)
+  constexpr int NY = M + 3;  // y differences phi(r) - phi(r+1), r = -2 .. M (index r + 2)
   const int lane = threadIdx.x & 31;
   const long long nwarps = (long long)gridDim.x * March3::WARPS;
   const long long wid = (long long)blockIdx.x * March3::WARPS + (threadIdx.x >> 5);
   long long ub = units * wid / nwarps;
   const long long ue = units * (wid + 1) / nwarps;
   const int nx = P.nx, ny = P.ny, nz = P.nz;
-  const int plane = nx * ny;
+  const int plane = nx * ny, N = (int)P.N;
   const float *__restrict__ ux = u;
   const float *__restrict__ uy = u + P.N;
   const float *__restrict__ uz = u + 2 * P.N;
+  // transfer coefficients in 2^-30 units: D of the z link, D / 36 and D / 6 of the smoothed x and
+  // y differences, 3 kappa / 216 on the smoothed compressive sums (a in real units)
   const float D = P.Dlap * (1.0f / 6.0f), Dx = D * (1.0f / 36.0f), Dy = D * (1.0f / 6.0f);
-  const float k3s = P.kc * kCs2 * 3.0f * (1.0f / 216.0f);
-  const float e72 = 72.0f * P.eps_n;
+  const float k3s_q = P.kc * kCs2 * 3.0f * (1.0f / 216.0f) * kQ30;
+  const float e72_q = 72.0f * P.eps_n * kQ30;
   const int gtx = (nx + 31) / 32, gty = (ny + 7) / 8;
 
   while (ub < ue) {
@@ -97,25 +110,40 @@ k_phase3m(const KParams P, const int32_t *__restrict__ phi, const float *__restr
     const int tx0 = xs / 32, tx1 = min(xs + March3::OUT - 1, nx - 1) / 32;
     unsigned tflag = 0;  // bit 0: tile tx0, bit 1: tile tx1, for the current group of 4 planes
 
-    float F0[NR], F1[NR], F2[NR], Fm[M];  // phi of planes p-2, p-1, p, and p-3 (rows 0..M-1)
-    float RZk[NA];                        // s_z phi of plane p-2, rows -1..M
-    float HX0[NA], HX1[NA], HY0[NA], HY1[NA];  // a_x, a_y of planes p-3, p-2, rows -1..M
-    float ASk[M], UZk[M];                 // s_x s_y a_z and u_z of plane p-2
-    int TZk[M];                           // transfer of the z face below plane p-2
+    int32_t I0[NR], I1[NR], NX[NR], Im[M];  // phi of planes p-2, p-1, next (p), and p-3 rows 0..M-1
+    float DX0[NR], DX1[NR];                 // phi(x) - phi(x+1) of planes p-2, p-1
+    float DY0[NY], DY1[NY];                 // phi(y) - phi(y+1) of planes p-2, p-1
+    float XYk[M], YZk[M + 1];               // s_y s_z (phi(x) - phi(x+1)), s_z (phi(y) - phi(y+1)), plane p-2
+    float HX0[NA], HX1[NA], HY0[NA], HY1[NA];  // a_x, a_y of planes p-3, p-2
+    float ASk[M], UZk[M];                   // s_x s_y a_z and u_z of plane p-2
+    int TZk[M];                             // transfer of the z face below plane p-2
 #pragma unroll
-    for (int i = 0; i < NR; i++) { F0[i] = 0.f; F1[i] = 0.f; }
+    for (int i = 0; i < NR; i++) { I0[i] = I1[i] = 0; DX0[i] = DX1[i] = 0.f; }
 #pragma unroll
-    for (int i = 0; i < NA; i++) { RZk[i] = 0.f; HX0[i] = HX1[i] = HY0[i] = HY1[i] = 0.f; }
+    for (int i = 0; i < NY; i++) DY0[i] = DY1[i] = 0.f;
 #pragma unroll
-    for (int r = 0; r < M; r++) { Fm[r] = 0.f; ASk[r] = 0.f; UZk[r] = 0.f; TZk[r] = 0; }
+    for (int i = 0; i < NA; i++) HX0[i] = HX1[i] = HY0[i] = HY1[i] = 0.f;
+#pragma unroll
+    for (int r = 0; r < M; r++) { Im[r] = 0; XYk[r] = 0.f; ASk[r] = 0.f; UZk[r] = 0.f; TZk[r] = 0; }
+#pragma unroll
+    for (int j = 0; j <= M; j++) YZk[j] = 0.f;
+
+    // plane offsets of p, p - 1, p - 2 (stepped, no division in the loop); phi of the first plane
+    int pz = wrapi(z0 - 2, nz) * plane;
+    int pz1 = (pz == 0 ? N : pz) - plane, pz2 = (pz1 == 0 ? N : pz1) - plane;
+#pragma unroll
+    for (int i = 0; i < NR; i++) NX[i] = __ldg(phi + pz + yo[i]);
 
     for (int p = z0 - 2; p <= z1 + 1; p++) {
-      const int pz = wrapi(p, nz) * plane;
-      // phi of plane p
+      int32_t I2[NR];
 #pragma unroll
-      for (int i = 0; i < NR; i++) F2[i] = phi_of(__ldg(phi + pz + yo[i]));
+      for (int i = 0; i < NR; i++) I2[i] = NX[i];
+      const int pzn = pz + plane == N ? 0 : pz + plane;
+      if (p < z1 + 1) {  // phi of the next plane, in flight during this iteration
+#pragma unroll
+        for (int i = 0; i < NR; i++) NX[i] = __ldg(phi + pzn + yo[i]);
+      }
       float uzn[M], uxk[M], uyk[NA];
-      const int pz1 = wrapi(p - 1, nz) * plane, pz2 = wrapi(p - 2, nz) * plane;
       if (p >= z0) {
 #pragma unroll
         for (int r = 0; r < M; r++) uzn[r] = __ldg(uz + pz1 + yo[r + 2]);
@@ -126,24 +154,35 @@ k_phase3m(const KParams P, const int32_t *__restrict__ phi, const float *__restr
 #pragma unroll
         for (int i = 0; i < NA; i++) uyk[i] = __ldg(uy + pz2 + yo[i + 1]);
       }
-      float RZ1[NR], ax[NA], ay[NA], ASn[M];
-      if (p >= z0) {
-        // a = phi (1 - phi) n at plane p - 1, rows -1..M
+      // exact differences of the new plane
+      float DXp[NR], DYp[NY];
 #pragma unroll
-        for (int i = 0; i < NR; i++) RZ1[i] = m141(F0[i], F1[i], F2[i]);
+      for (int i = 0; i < NR; i++) DXp[i] = i2f(I2[i] - sh_dn_i(I2[i]));
+#pragma unroll
+      for (int j = 0; j < NY; j++) DYp[j] = i2f(I2[j] - I2[j + 1]);
+
+      float XYZ[NA], YZ[NY], ax[NA], ay[NA], ASn[M];
+      if (p >= z0) {
+        // a = phi (1 - phi) n at plane p - 1, rows -1..M; G = 72 grad(phi) in 2^-30 units
+        float XZ[NR];
+#pragma unroll
+        for (int i = 0; i < NR; i++) XZ[i] = m141(DX0[i], DX1[i], DXp[i]);
+#pragma unroll
+        for (int i = 0; i < NA; i++) XYZ[i] = m141(XZ[i], XZ[i + 1], XZ[i + 2]);
+#pragma unroll
+        for (int j = 0; j < NY; j++) YZ[j] = m141(DY0[j], DY1[j], DYp[j]);
         float az[NA];
 #pragma unroll
         for (int i = 0; i < NA; i++) {
-          const float syr = m141(RZ1[i], RZ1[i + 1], RZ1[i + 2]);
-          const float gx = sh_dn(syr) - sh_up(syr);
-          const float dy = RZ1[i + 2] - RZ1[i];
-          const float gy = m141(sh_up(dy), dy, sh_dn(dy));
-          const float syd = m141(F2[i] - F0[i], F2[i + 1] - F0[i + 1], F2[i + 2] - F0[i + 2]);
-          const float gz = m141(sh_up(syd), syd, sh_dn(syd));
-          const float ph = F1[i + 1];
+          const float gx = -(XYZ[i] + sh_up(XYZ[i]));       // s_y s_z (phi(x+1) - phi(x-1))
+          const float cy = -(YZ[i] + YZ[i + 1]);            // s_z (phi(y+1) - phi(y-1))
+          const float gy = m141(sh_up(cy), cy, sh_dn(cy));
+          const float sz = m141(i2f(I2[i] - I0[i]), i2f(I2[i + 1] - I0[i + 1]), i2f(I2[i + 2] - I0[i + 2]));
+          const float gz = m141(sh_up(sz), sz, sh_dn(sz));
+          const float ph = i2f(I1[i + 1]) * kInvQ30;
           const float gg = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
           const float gn = gg > 0.0f ? gg * rsqrtf(gg) : 0.0f;
-          const float sc = __fdividef(ph * (1.0f - ph), gn + e72);
+          const float sc = __fdividef(ph * (1.0f - ph), gn + e72_q);
           ax[i] = gx * sc;
           ay[i] = gy * sc;
           az[i] = gz * sc;
@@ -159,10 +198,10 @@ k_phase3m(const KParams P, const int32_t *__restrict__ phi, const float *__restr
         // z face between planes p-2 and p-1, rows 0..M-1
 #pragma unroll
         for (int r = 0; r < M; r++) {
-          const float v0 = F0[r + 2], v1 = F1[r + 2];
+          const int32_t v0 = I0[r + 2], v1 = I1[r + 2];
           const float uf = 0.5f * (UZk[r] + uzn[r]);
-          const float up = upw(uf, Fm[r], v0, v1, F2[r + 2]);
-          TZn[r] = __float2int_rn(kQ30 * fmaf(D, v0 - v1, fmaf(k3s, ASk[r] + ASn[r], uf * up)));
+          const float up = upw_i(uf, Im[r], v0, v1, I2[r + 2]);
+          TZn[r] = __float2int_rn(fmaf(D, i2f(v0 - v1), fmaf(k3s_q, ASk[r] + ASn[r], uf * up)));
         }
       }
       if (p >= z0 + 2) {
@@ -171,14 +210,12 @@ k_phase3m(const KParams P, const int32_t *__restrict__ phi, const float *__restr
         int TX[M], TY[M + 1];
 #pragma unroll
         for (int r = 0; r < M; r++) {
-          const float T = m141(RZk[r], RZk[r + 1], RZk[r + 2]);
           const float AX = m141(m141(HX0[r], HX1[r], ax[r]), m141(HX0[r + 1], HX1[r + 1], ax[r + 1]),
                                 m141(HX0[r + 2], HX1[r + 2], ax[r + 2]));
-          const float v0 = F0[r + 2];
-          const float vm = sh_up(v0), v1 = sh_dn(v0), vp = sh_dn2(v0);
+          const int32_t v0 = I0[r + 2];
           const float uf = 0.5f * (uxk[r] + sh_dn(uxk[r]));
-          const float up = upw(uf, vm, v0, v1, vp);
-          TX[r] = __float2int_rn(kQ30 * fmaf(Dx, T - sh_dn(T), fmaf(k3s, AX + sh_dn(AX), uf * up)));
+          const float up = upw_i(uf, sh_up_i(v0), v0, sh_dn_i(v0), sh_dn2_i(v0));
+          TX[r] = __float2int_rn(fmaf(Dx, XYk[r], fmaf(k3s_q, AX + sh_dn(AX), uf * up)));
         }
         float AY[NA];
 #pragma unroll
@@ -189,17 +226,16 @@ k_phase3m(const KParams P, const int32_t *__restrict__ phi, const float *__restr
 #pragma unroll
         for (int j = 0; j < M + 1; j++) {  // face between rows j - 1 and j
           const float uf = 0.5f * (uyk[j] + uyk[j + 1]);
-          const float up = upw(uf, F0[j], F0[j + 1], F0[j + 2], F0[j + 3]);
-          TY[j] = __float2int_rn(kQ30 * fmaf(Dy, RZk[j] - RZk[j + 1], fmaf(k3s, AY[j] + AY[j + 1], uf * up)));
+          const float up = upw_i(uf, I0[j], I0[j + 1], I0[j + 2], I0[j + 3]);
+          TY[j] = __float2int_rn(fmaf(Dy, YZk[j], fmaf(k3s_q, AY[j] + AY[j + 1], uf * up)));
         }
-        const int kz = wrapi(k, nz) * plane;
         bool g0 = false, g1 = false;
 #pragma unroll
         for (int r = 0; r < M; r++) {
           const int acc = sh_up_i(TX[r]) - TX[r] + TY[r] - TY[r + 1] + TZk[r] - TZn[r];
           if (xout && ys + r < ny) {
-            const int32_t vn = __ldg(phi + kz + yo[r + 2]) + acc;
-            phi_out[kz + yo[r + 2]] = vn;
+            const int32_t vn = I0[r + 2] + acc;
+            phi_out[pz2 + yo[r + 2]] = vn;
             if (tiles && q_gate_value(vn) >= P.q_th) {
               if ((xs + lane - 2) / 32 == tx0) g0 = true; else g1 = true;
             }
@@ -223,18 +259,22 @@ k_phase3m(const KParams P, const int32_t *__restrict__ phi, const float *__restr
       }
       if (p >= z0) {
 #pragma unroll
-        for (int r = 0; r < M; r++) { ASk[r] = ASn[r]; UZk[r] = uzn[r]; }
+        for (int r = 0; r < M; r++) { ASk[r] = ASn[r]; UZk[r] = uzn[r]; XYk[r] = XYZ[r + 1]; }
+#pragma unroll
+        for (int j = 0; j <= M; j++) YZk[j] = YZ[j + 1];
 #pragma unroll
         for (int i = 0; i < NA; i++) {
-          RZk[i] = RZ1[i + 1];
           HX0[i] = HX1[i]; HX1[i] = ax[i];
           HY0[i] = HY1[i]; HY1[i] = ay[i];
         }
       }
 #pragma unroll
-      for (int r = 0; r < M; r++) Fm[r] = F0[r + 2];
+      for (int r = 0; r < M; r++) Im[r] = I0[r + 2];
 #pragma unroll
-      for (int i = 0; i < NR; i++) { F0[i] = F1[i]; F1[i] = F2[i]; }
+      for (int i = 0; i < NR; i++) { I0[i] = I1[i]; I1[i] = I2[i]; DX0[i] = DX1[i]; DX1[i] = DXp[i]; }
+#pragma unroll
+      for (int j = 0; j < NY; j++) { DY0[j] = DY1[j]; DY1[j] = DYp[j]; }
+      pz2 = pz1; pz1 = pz; pz = pzn;
     }
   }
 }
