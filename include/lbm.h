@@ -184,6 +184,31 @@ int lbm_energy_spectrum(lbm_ctx *ctx, int nshells, double *E);
  * *out receives the batch; on error nothing is allocated. */
 typedef struct lbm_batch lbm_batch;
 int lbm_batch_create(lbm_ctx *const *ctxs, int n, int nstreams, void *stream, lbm_batch **out);
+/* lbm_batch_create with flags. Without flags, when every context is 3D with one lattice (19 or 27)
+ * and one store type, nx even and Q N <= 2^32, the batch runs FUSED: per step, the near-contact
+ * pass of each context on the concurrent branches, then one launch of the hydrodynamic pass and
+ * one launch of the phase-field pass over all contexts together (persistent grids walking a work
+ * list of every case's tiles), with the same per-cell arithmetic as lbm_step, so the results are
+ * identical. An autotuner then times, on the contexts' own state and without changing it, the
+ * hydrodynamic tile shape (64 x ty x 8/ty cells, ty = 4, 2, 8) and the rows of y per thread of the
+ * phase-field march (4 or 2), keeps the fastest, and finally times one step of that fused
+ * execution against one step of the per-case graph and keeps the faster (lbm_batch_config).
+ * Otherwise, or with LBM_BATCH_PER_CASE, the graph holds every context's own steps on the branches.
+ * LBM_BATCH_NO_TUNE keeps ty = 4 and 4 rows; LBM_BATCH_HYDRO_TY2 / _TY8 and LBM_BATCH_PHASE_ROWS2
+ * pin those choices instead (no tuning). Creation allocates the work lists (8 B per tile) and a
+ * case table; unknown or contradictory flags: LBM_ERR_ARG. */
+#define LBM_BATCH_PER_CASE 1
+#define LBM_BATCH_NO_TUNE 2
+#define LBM_BATCH_HYDRO_TY2 4
+#define LBM_BATCH_HYDRO_TY8 8
+#define LBM_BATCH_PHASE_ROWS2 16
+int lbm_batch_create_ex(lbm_ctx *const *ctxs, int n, int nstreams, void *stream, int flags, lbm_batch **out);
+/* The batch's configuration: cfg (8 ints, may be NULL) = fused (1/0), hydrodynamic tile ty, tz,
+ * phase-field rows per thread, branches, hydrodynamic blocks, phase-field blocks, hydrodynamic
+ * work items; ms (7 doubles, may be NULL) = the tuner's time per pass of the hydrodynamic
+ * candidates ty = 4, 2, 8 and of the phase-field candidates rows = 4, 2, then of one step of the
+ * fused and of the per-case execution (0 when not tuned). */
+int lbm_batch_config(const lbm_batch *b, int *cfg, double *ms);
 /* Advances every context by nsteps: one graph launch per two steps, and for an odd nsteps a last
  * plain step of each context, all on the batch's launch stream. Asynchronous like lbm_step:
  * synchronise the launch stream (or call lbm_batch_synchronize) before reading results. Two graphs

@@ -76,6 +76,8 @@ def load():
     L.lbm_curvature.argtypes = [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_int, _VP, _VP]
     L.lbm_energy_spectrum.argtypes = [_VP, ctypes.c_int, _VP]
     L.lbm_batch_create.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.POINTER(_VP)]
+    L.lbm_batch_create_ex.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, ctypes.POINTER(_VP)]
+    L.lbm_batch_config.argtypes = [_VP, _VP, _VP]
     L.lbm_batch_step.argtypes = [_VP, ctypes.c_int]
     L.lbm_batch_synchronize.argtypes = [_VP]
     L.lbm_batch_destroy.argtypes = [_VP]
@@ -92,6 +94,7 @@ def load():
     for name in ("lbm_create", "lbm_set_stream", "lbm_init_fields", "lbm_set_state", "lbm_get_state",
                  "lbm_step", "lbm_read_fields", "lbm_mass", "lbm_mass_noalloc", "lbm_read_nci", "lbm_synchronize",
                  "lbm_profile", "lbm_profile_kinds", "lbm_profile_read", "lbm_lattice", "lbm_batch_create", "lbm_batch_step",
+                 "lbm_batch_create_ex", "lbm_batch_config",
                  "lbm_nci_diagnostics", "lbm_curvature", "lbm_energy_spectrum",
                  "lbm_batch_synchronize"):
         getattr(L, name).restype = ctypes.c_int
@@ -281,12 +284,35 @@ def lbm_lattice(dim: int, Q: int):
     return c, w
 
 
+LBM_BATCH_PER_CASE, LBM_BATCH_NO_TUNE, LBM_BATCH_HYDRO_TY2, LBM_BATCH_HYDRO_TY8, LBM_BATCH_PHASE_ROWS2 = 1, 2, 4, 8, 16
+
+
 def lbm_batch_create(ctxs, nstreams: int = 8, stream: int = 0) -> int:
     arr = (_VP * len(ctxs))(*[_VP(c) for c in ctxs])
     h = _VP()
     _check(load().lbm_batch_create(arr, len(ctxs), int(nstreams), _VP(stream or None), ctypes.byref(h)),
            "lbm_batch_create")
     return h.value
+
+
+def lbm_batch_create_ex(ctxs, nstreams: int = 8, stream: int = 0, flags: int = 0) -> int:
+    arr = (_VP * len(ctxs))(*[_VP(c) for c in ctxs])
+    h = _VP()
+    _check(load().lbm_batch_create_ex(arr, len(ctxs), int(nstreams), _VP(stream or None), int(flags),
+                                      ctypes.byref(h)), "lbm_batch_create_ex")
+    return h.value
+
+
+def lbm_batch_config(batch: int) -> dict:
+    cfg = np.zeros(8, dtype=np.int32)
+    ms = np.zeros(7)
+    _check(load().lbm_batch_config(_VP(batch), cfg.ctypes.data_as(_VP), ms.ctypes.data_as(_VP)), "lbm_batch_config")
+    keys = ("fused", "hydro_ty", "hydro_tz", "phase_rows", "branches", "hydro_blocks", "phase_blocks", "hydro_items")
+    d = {k: int(v) for k, v in zip(keys, cfg)}
+    d["tune_ms"] = {"hydro_ty4": float(ms[0]), "hydro_ty2": float(ms[1]), "hydro_ty8": float(ms[2]),
+                    "phase_rows4": float(ms[3]), "phase_rows2": float(ms[4]),
+                    "step_fused": float(ms[5]), "step_per_case": float(ms[6])}
+    return d
 
 
 def lbm_batch_step(batch: int, n: int) -> None:
@@ -305,9 +331,12 @@ def lbm_batch_destroy(batch: int) -> None:
 class LbmBatch:
     """Independent contexts advanced together through one CUDA graph (keeps the contexts alive)."""
 
-    def __init__(self, sims, nstreams: int = 8, stream: int = 0):
+    def __init__(self, sims, nstreams: int = 8, stream: int = 0, flags: int = 0):
         self.sims = list(sims)
-        self.h = lbm_batch_create([s.ctx for s in self.sims], nstreams, stream)
+        self.h = lbm_batch_create_ex([s.ctx for s in self.sims], nstreams, stream, flags)
+
+    def config(self) -> dict:
+        return lbm_batch_config(self.h)
 
     def step(self, n: int = 2, sync: bool = True):
         """Advances every context by n steps; with ``sync`` waits for the work (so that the

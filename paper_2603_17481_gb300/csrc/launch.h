@@ -71,6 +71,42 @@ cudaError_t launch_phase(int dim, const KParams &P, const int32_t *phi, const fl
 cudaError_t launch_gate_tiles(int dim, const KParams &P, const int32_t *phi, int *tiles, int *ntiles, cudaStream_t s);
 int tile_count(int dim, const KParams &P);
 
+// Geometry of the 3D phase-field register march (phase3_march.cuh).
+struct March3 {
+  static constexpr int OUT = 28;       // output columns per warp
+  static constexpr int WARPS = 4;      // warps per block
+  static constexpr int NT = 32 * WARPS;
+  static constexpr int MIN_RUN = 8;    // fewest planes per warp before the grid is shrunk
+};
+
+// Batched passes over many independent cases (the sweep of uneven collision cases). One
+// BatchCase per case and buffer parity: where the pass reads and writes, and its tile grids.
+struct __align__(16) BatchCase {
+  KParams P;
+  const void *src;      // populations of the current state
+  void *dst;            // populations of the next state
+  const int32_t *phi;   // phi^n
+  int32_t *phi_out;     // phi^{n+1}
+  const float4 *frep;   // near-contact force at the gated cells of phi^n
+  float *u;             // velocity, written by the hydrodynamic pass, read by the phase pass
+  int *reset;           // count of the near-contact list of phi^n (cleared by hydro), or null
+  int *tiles, *ntiles;  // near-contact list of phi^{n+1} (appended by the phase pass), or null
+  int *lflag;           // marks of the listed tiles
+  int ncx;              // x segments of the phase march
+  int pad;
+};
+// The paired hydrodynamic kernel over a list of (case, bx, by, bz) tile items of 64 x ty x tz cells
+// (ty x tz = 8; all cases D3Q19 or D3Q27 per Q, one store type, nx even, Q N <= 2^32), on a grid of
+// `blocks` resident blocks walking the list.
+cudaError_t launch_hydro_batch(int Q, int store, int ty, const BatchCase *cases, const int4 *items, int nitems,
+                               int blocks, cudaStream_t s);
+int hydro_batch_blocks(int Q, int store, int ty);  // resident blocks of the device (SMs x per SM)
+// The phase march over the concatenated (column, plane) units of every case (uoff: ncases + 1
+// prefix offsets); rows = 2 or 4 rows of y per thread.
+cudaError_t launch_phase_batch(int rows, const BatchCase *cases, const long long *uoff, int ncases, int blocks,
+                               cudaStream_t s);
+int phase_batch_blocks(int rows);
+
 // Conversions between host-layout FP64 staging buffers and the device state.
 cudaError_t launch_phi_in(const KParams &P, const double *phi64, int32_t *phi, cudaStream_t s);
 cudaError_t launch_phi_out(const KParams &P, const int32_t *phi, double *phi64, cudaStream_t s);

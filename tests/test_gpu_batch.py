@@ -71,6 +71,80 @@ def test_batch_matches_per_case_steps(nstreams):
         s.close()
 
 
+def _uniform_3d_cases(Q=19):
+    """Uneven 3D cases of one lattice (x sides even), near-contact on and off: the fused batch."""
+    cases = []
+    for i, (L, nci) in enumerate(((24, 1), (40, 1), (32, 0), (20, 1), (36, 1), (28, 1))):
+        cfg = W.collision_sweep(1, seed=200 + i, grids=(L,))[0]
+        cfg["nci_on"] = nci
+        cfg["Q"] = Q
+        cases.append(cfg)
+    c = W.base_config(3, 48, 22, 17, Q, rho_g=0.1)  # ragged y and z tiles
+    phi, u = W.droplet_fields(c, [(14.5, 10.5, 8.0), (33.0, 11.5, 8.5)], [6.0, 6.0], [(0.02, 0, 0), (-0.02, 0, 0)])
+    cases.append((c, phi, u))
+    return cases
+
+
+@pytest.mark.parametrize("Q,store,flags", [(19, "f32", 0), (19, "f16", 0), (27, "f32", 0), (19, "f32", 2), (19, "f32", 4),
+                                           (19, "f32", 8), (19, "f32", 16), (19, "f16", 4 | 16)])
+def test_fused_batch_matches_per_case_steps(Q, store, flags):
+    """One launch per pass over all cases (fused mode, tuned or not): the same states, bit for bit,
+    as per-case lbm_step calls, through even and odd step counts in both buffer parities."""
+    single, batched = [], []
+    for c in _uniform_3d_cases(Q):
+        cfg, phi, u = c if isinstance(c, tuple) else (c, *W.sweep_case_fields(c))
+        for lst in (single, batched):
+            s = B.Lbm(cfg, store=store)
+            s.init_fields(phi, u)
+            lst.append(s)
+    batch = B.LbmBatch(batched, nstreams=4, flags=flags)
+    cfg = batch.config()
+    assert cfg["hydro_ty"] in (2, 4, 8) and cfg["phase_rows"] in (2, 4)
+    if flags:
+        assert cfg["fused"] == 1
+        assert cfg["hydro_ty"] == (2 if flags & 4 else (8 if flags & 8 else 4))
+        assert cfg["phase_rows"] == (2 if flags & 16 else 4)
+    else:
+        t = cfg["tune_ms"]
+        assert all(v > 0 for v in t.values())
+        assert cfg["fused"] == (1 if t["step_fused"] <= t["step_per_case"] else 0)
+    for n in (4, 3, 0, 1, 3, 2, 1, 6):
+        batch.step(n)
+        for s in single:
+            s.step(n)
+        for a, b in zip(_states(single), _states(batched)):
+            assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    for a, b in zip(single, batched):
+        ma, pa = a.mass()
+        mb, pb = b.mass()
+        assert ma == mb and np.array_equal(pa, pb)
+    batch.close()
+    for s in single + batched:
+        s.close()
+
+
+def test_batch_modes():
+    """Mixed 2D / 3D cases, or the per-case flag, give the per-case graph; uniform 3D cases fuse."""
+    mixed = [B.Lbm(c) for c in _small_cases()[:2]] + [B.Lbm(W.base_config(2, 30, 20, 1, 9))]
+    for s in mixed:
+        N = W.ncells(s.cfg)
+        s.init_fields(np.zeros(N), np.zeros((3, N)))
+    b = B.LbmBatch(mixed, nstreams=2)
+    assert b.config()["fused"] == 0
+    b.close()
+    b = B.LbmBatch(mixed[:2], nstreams=2, flags=B.LBM_BATCH_PER_CASE)
+    assert b.config()["fused"] == 0
+    b.close()
+    b = B.LbmBatch(mixed[:2], nstreams=2, flags=B.LBM_BATCH_NO_TUNE)
+    assert b.config()["fused"] == 1
+    b.close()
+    for bad in (32, 4 | 8):
+        with pytest.raises(B.LbmError):
+            B.LbmBatch(mixed[:2], nstreams=2, flags=bad)
+    for s in mixed:
+        s.close()
+
+
 def test_batch_case_against_oracle():
     """A 40^3 sweep case advanced 20 steps inside a batch of three against the FP64 oracle."""
     cfgs = [W.collision_sweep(1, seed=s, grids=(L,))[0] for s, L in ((3, 40), (4, 24), (5, 32))]
