@@ -420,8 +420,9 @@ SWEEP_WORKLOAD = ("batched sweep: {n} independent 3D D3Q19 collisions on grids d
 
 
 def run_sweep(args, world, rank, local):
-    """The batched sweep: every case advanced through one CUDA graph per two steps (lbm_batch_step),
-    against the same cases advanced by per-case lbm_step calls, one case after another."""
+    """The batched sweep: every case advanced through one CUDA graph per two steps (lbm_batch_step):
+    fused (one launch per pass over all cases, autotuned) and as a graph of per-case steps, against
+    the same cases advanced by per-case lbm_step calls, one case after another."""
     import numpy as np
     import torch
 
@@ -441,7 +442,8 @@ def run_sweep(args, world, rank, local):
         m0.append(s.mass()[0])
         sims.append(s)
     cells = sum(s.N for s in sims)
-    launches_per_step = sum(kernels_per_step(c) for c in cfgs)
+    launches_fused = sum(kernels_per_step(c) - 2 for c in cfgs) + 2  # near-contact per case, 2 batched
+    launches_case = sum(kernels_per_step(c) for c in cfgs)
     steps = args.steps + (args.steps & 1)  # whole graph launches
 
     def timed(run, k):
@@ -463,21 +465,29 @@ def run_sweep(args, world, rank, local):
     ms_single = timed(per_case, steps)
     mlups_single, ms_single_max = whole_job_mlups(world, cells, steps, ms_single, device=f"cuda:{local}")
 
-    results = {}
+    # the per-case graph (every context's own steps on concurrent branches), the fused batch as is
+    # (one launch per pass over all cases, tile shape 64x4x2 and 4 march rows), and the autotuned
+    # batch (tile shape and march rows tuned, then the faster of fused and per-case), at each
+    # branch count
+    results, graph_results, fused_results, configs = {}, {}, {}, {}
     sampler = ClockSampler(local)
     for ns in args.streams:
-        batch = B.LbmBatch(sims, nstreams=ns, stream=stream.cuda_stream)
-        batch.step(args.warmup + (args.warmup & 1), sync=True)
-        if ns == args.streams[-1]:
-            sampler.start()
-            time.sleep(0.3)
-        ms = timed(lambda k: batch.step(k, sync=False), steps)
-        results[ns] = whole_job_mlups(world, cells, steps, ms, device=f"cuda:{local}")
-        batch.close()
+        for mode in ("graph", "fused", "tuned"):
+            flags = {"graph": B.LBM_BATCH_PER_CASE, "fused": B.LBM_BATCH_NO_TUNE, "tuned": 0}[mode]
+            batch = B.LbmBatch(sims, nstreams=ns, stream=stream.cuda_stream, flags=flags)
+            batch.step(args.warmup + (args.warmup & 1), sync=True)
+            if mode == "tuned" and ns == args.streams[-1]:
+                sampler.start()
+                time.sleep(0.3)
+            ms = timed(lambda k: batch.step(k, sync=False), steps)
+            {"graph": graph_results, "fused": fused_results, "tuned": results}[mode][ns] = whole_job_mlups(
+                world, cells, steps, ms, device=f"cuda:{local}")
+            if mode == "tuned":
+                configs[ns] = batch.config()
+            batch.close()
     clocks = sampler.stop()
     best = max(results, key=lambda ns: results[ns][0])
     mlups, ms_max = results[best]
-
     drift, nonfinite = 0.0, 0
     for s, m in zip(sims, m0):
         m1, _ = s.mass()
@@ -503,10 +513,17 @@ def run_sweep(args, world, rank, local):
                               "ms_per_step": round(ms_single_max / steps, 5),
                               "what": "lbm_step(K) per case, cases one after another on one stream"},
         "batched_vs_per_case": round(mlups / mlups_single, 3),
-        "by_graph_branches": {str(ns): round(v[0], 1) for ns, v in results.items()},
+        "per_case_graph": {"by_branches": {str(ns): round(v[0], 1) for ns, v in graph_results.items()},
+                           "what": "CUDA graph of every case's own lbm_step kernels on concurrent branches"},
+        "fused_untuned": {"by_branches": {str(ns): round(v[0], 1) for ns, v in fused_results.items()},
+                          "what": "one hydrodynamic and one phase-field launch over all cases per step, "
+                                  "64x4x2 tiles, 4 march rows"},
+        "tuned_by_branches": {str(ns): round(v[0], 1) for ns, v in results.items()},
+        "tuned_config": configs[best],
+        "tuned_vs_per_case_graph": round(mlups / max(v[0] for v in graph_results.values()), 3),
         "step_roofline": {"bytes_per_cell": step_bytes_per_cell(19, 4), "frac_of_measured": round(frac, 4),
                           "peak": peak, "peak_source": peak_kind},
-        "gpu_launches": launches_per_step * steps,
+        "gpu_launches": (launches_fused if configs[best]["fused"] else launches_case) * steps,
         "clocks": clocks,
         "phi_mass_drift_max": drift, "nonfinite_cases": nonfinite,
     }
@@ -645,6 +662,70 @@ def run_swarm(args, world, rank, local):
     }
 
 
+IMPACT_WORKLOAD = ("the paper's {case} droplet impact, {L}^3 periodic D3Q19, D_lu = {D:g}, density ratio 1000, "
+                   "sigma = 0.02, We = {we}, B = {B}, nu_l = {nul}, nu_g = {nug}")
+
+
+def run_impact(args, world, rank, local):
+    """The paper's droplet impacts of Sec. 3.1 (E1 head-on We 4.6, E2 off-axis We 4.8, B 0.32) at
+    density ratio 1000 as synthetic stress workloads: throughput of the FP32 and FP16-store paths,
+    exact phi mass and finite fields after the timed steps."""
+    import numpy as np
+    import torch
+
+    from paper_2603_17481_gb300 import binding as B
+    from paper_2603_17481_gb300 import build as lbm_build
+    from paper_2603_17481_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    lbm_build.build()
+    cfg, phi, u = W.droplets_paper_impact(args.case, L=args.impact_L, D=args.impact_D)
+    phi = W.to_q30_grid(phi)
+    N = W.ncells(cfg)
+    stream = torch.cuda.Stream()
+    runs = {}
+    for store in ("f32", "f16"):
+        sim = B.Lbm(cfg, store=store, stream=stream.cuda_stream)
+        sim.init_fields(phi, u)
+        m0, _ = sim.mass()
+        sim.step(args.warmup)
+        sim.synchronize()
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            sim.step(1)
+        e1.record(stream)
+        e1.synchronize()
+        barrier(world)
+        mlups, ms_max = whole_job_mlups(world, N, args.steps, e0.elapsed_time(e1), device=f"cuda:{local}")
+        m1, mom = sim.mass()
+        ph, uu, _ = sim.read_fields(want=("phi", "u"))
+        runs[store] = {"value": round(mlups, 1), "ms_per_step": round(ms_max / args.steps, 5),
+                       "phi_mass_drift": abs(m1 - m0) / abs(m0), "finite": bool(np.all(np.isfinite(uu))),
+                       "max_u": float(np.max(np.abs(uu))), "after_steps": args.warmup + args.steps}
+        sim.close()
+    if rank != 0:
+        return None
+    peak, peak_kind = measured_peaks()
+    v = runs["f32"]["value"]
+    return {
+        "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": runs["f32"]["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": IMPACT_WORKLOAD.format(case=args.case, L=args.impact_L, D=args.impact_D, we=cfg["We"],
+                                                      B=cfg["B"], nul=cfg["nu_l"], nug=cfg["nu_g"]),
+                   "cells": N, "l2": "inputs larger than L2, no flush",
+                   "parallelism": f"{world} independent replica(s), one per GPU"},
+        "step_roofline": {"bytes_per_cell": step_bytes_per_cell(19, 4),
+                          "frac_of_measured": round(v / world * 1e6 * step_bytes_per_cell(19, 4) / (peak * 1e9), 4),
+                          "peak": peak, "peak_source": peak_kind},
+        "runs": runs,
+        "gpu_launches": int(kernels_per_step(cfg) * args.steps),
+    }
+
+
 def run_selftune(args, world, rank, local):
     """Film statistics over D x sigma x A_rep / sigma (Sec. 3.3): every case advanced in one batch,
     lbm_nci_diagnostics every --diag-every steps, each case's record taken at its maximum film
@@ -772,10 +853,11 @@ def parse_args(argv=None):
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=120.0, help="seconds for the whole reference arm")
-    ap.add_argument("--workload", choices=["collision", "sweep", "swarm", "selftune"], default="collision",
+    ap.add_argument("--workload", choices=["collision", "sweep", "swarm", "selftune", "impact"], default="collision",
                     help="collision: the 256x128x128 head-on case; sweep: the batched sweep of independent "
                          "cases; swarm: the 512^3 bubble swarm with the near-contact repulsion on and off; "
-                         "selftune: film statistics over D x sigma x A_rep")
+                         "selftune: film statistics over D x sigma x A_rep; impact: the paper's E1/E2 "
+                         "droplet impacts at density ratio 1000")
     ap.add_argument("--cases", type=int, default=512, help="sweep: number of cases")
     ap.add_argument("--streams", type=int, nargs="+", default=[16], help="sweep: graph branch counts to time")
     ap.add_argument("--swarm-L", type=int, default=512)
@@ -784,6 +866,9 @@ def parse_args(argv=None):
     ap.add_argument("--swarm-count-at", type=int, nargs="*", default=[], help="swarm: also count bubbles at these steps")
     ap.add_argument("--swarm-gap", type=float, default=2.0, help="swarm: minimum initial surface gap in units of eps")
     ap.add_argument("--diag-every", type=int, default=20, help="selftune: steps between film statistics")
+    ap.add_argument("--case", choices=["E1", "E2"], default="E1", help="impact: which of the paper's impacts")
+    ap.add_argument("--impact-L", type=int, default=512, help="impact: periodic box edge")
+    ap.add_argument("--impact-D", type=float, default=80.0, help="impact: droplet diameter in lattice units")
     args = ap.parse_args(argv)
     if args.steps < 1 or args.warmup < 0:
         ap.error("--steps must be >= 1 and --warmup >= 0")
@@ -801,6 +886,8 @@ def main():
         line = run_swarm(args, world, rank, local)
     elif args.workload == "selftune":
         line = run_selftune(args, world, rank, local)
+    elif args.workload == "impact":
+        line = run_impact(args, world, rank, local)
     else:
         line = run_ours(args, world, rank, local)
     if rank == 0 and line is not None:

@@ -408,3 +408,70 @@ def test_paper_impacts_density_ratio_1000_stable(case):
     g = phg.reshape(cfg["nz"], cfg["ny"], cfg["nx"])
     assert g[:, :, :cfg["nx"] // 2].max() > 0.5 and g[:, :, cfg["nx"] // 2:].max() > 0.5
     sim.close()
+@pytest.fixture(scope="module")
+def c3_oracle():
+    """The FP64 oracle's phi and velocity on the full 256x128x128 ratio-100 collision after 50, 100
+    and 200 steps (about four minutes of host time, shared by the tests below)."""
+    cfg, phi, u = W.droplets_head_on_3d()
+    phi = W.to_q30_grid(phi)
+    P = O.make_params(cfg)
+    f = O.init(P, phi, u)
+    out, ph, done = {}, phi, 0
+    for k in (50, 100, 200):
+        f, ph, _ = O.step(P, f, ph, k - done)
+        done = k
+        _, uo = O.moments(P, f, ph)
+        out[k] = (ph.copy(), uo)
+    return cfg, phi, u, out
+
+
+def _c3_check(cfg, phi, u, ref, store, tmax, tq999, tu):
+    sim = B.Lbm(cfg, store=store)
+    sim.init_fields(phi, u)
+    m0, _ = sim.mass()
+    done, fails = 0, []
+    for k in (50, 100, 200):
+        sim.step(k - done)
+        done = k
+        phg, ug, _ = sim.read_fields(want=("phi", "u"))
+        pho, uo = ref[k]
+        d = np.abs(phg - pho)
+        dmax, dq = float(d.max()), float(np.quantile(d, 0.999))
+        du = float(np.max(np.abs(ug - uo)))
+        dc = float(np.max(np.abs(_half_box_centroids(cfg, phg) - _half_box_centroids(cfg, pho))))
+        print(f"[parity] C3 {store} step {k}: max|dphi|={dmax:.3e} q999={dq:.3e} max|du|={du:.3e} centroids {dc:.2e}")
+        if k in tmax and dmax > tmax[k]:
+            fails.append(f"step {k}: max|dphi| {dmax:.3e} > {tmax[k]}")
+        if k in tq999 and dq > tq999[k]:
+            fails.append(f"step {k}: 99.9th percentile of |dphi| {dq:.3e} > {tq999[k]}")
+        if k in tu and du > tu[k]:
+            fails.append(f"step {k}: max|du| {du:.3e} > {tu[k]}")
+        if k == 200 and dc > 0.05:
+            fails.append(f"step {k}: centroid error {dc:.3e} cells > 0.05")
+    m1, _ = sim.mass()
+    sim.close()
+    assert m1 == m0, "phi mass changed"
+    assert not fails, "; ".join(fails)
+
+
+def test_full_size_fp32_against_fp64_oracle(c3_oracle):
+    """The benchmark's collision at full size (256x128x128 D3Q19, ratio 100, the bench's launch
+    configuration) in FP32 against the FP64 oracle: max|dphi| <= 1e-5 and max|du| <= 1e-6 at steps 50
+    and 100; at step 200, after the films have formed and the facing decisions in the mirror-symmetric
+    film make the two trajectories part pointwise, the 99.9th percentile of |dphi| <= 1e-5 and the
+    droplet centroids within 0.05 cells; phi mass exact."""
+    cfg, phi, u, ref = c3_oracle
+    _c3_check(cfg, phi, u, ref, "f32", {50: 1e-5, 100: 1e-5}, {200: 1e-5}, {50: 1e-6, 100: 1e-6})
+
+
+@pytest.mark.parametrize("store", ["f16", pytest.param("bf16", marks=pytest.mark.xfail(
+    strict=True, reason="BF16 storage misses the 1e-3 phi target: 99.9th percentile 1.3e-3 at step 100"))])
+def test_full_size_half_store_against_fp64_oracle(c3_oracle, store):
+    """FP16 and BF16 population storage on the full-size collision against the FP64 oracle: max|dphi|
+    <= 1e-3 at step 50; the 99.9th percentile of |dphi| <= 1e-3 at steps 100 and 200 (from about
+    step 75 the droplet interiors, where phi departs from 1 by ~1 % and |grad phi| is comparable
+    to eps_n, turn any perturbation of the size that half-precision storage makes into a local
+    compressive flux of up to ~1e-3 per step); droplet centroids within 0.05 cells at step 200;
+    phi mass exact."""
+    cfg, phi, u, ref = c3_oracle
+    _c3_check(cfg, phi, u, ref, store, {50: 1e-3}, {100: 1e-3, 200: 1e-3}, {})
