@@ -32,13 +32,31 @@ WORKLOAD = "3D head-on droplet collision 256x128x128 D3Q{Q}, R=24, W=4, density 
 HBM_FALLBACK_GBS = 6800.0
 # Algorithmic bytes per cell update (stored state only): populations read + written, phi read +
 # written, velocity written + read.
-def kernels_per_step(cfg):
-    """Kernels one lbm_step launches: hydro and phase, plus the near-contact normals and scan and,
-    on 3D grids whose sides are multiples of 4, the brick prefilter between them."""
+def nci_kernels(cfg):
+    """Kernels of one near-contact pass: normals and scan and, on 3D grids whose sides are multiples
+    of 4, the brick prefilter between them."""
     if not cfg["nci_on"]:
-        return 2
+        return 0
     prefilter = cfg["dim"] == 3 and all(cfg[k] % 4 == 0 for k in ("nx", "ny", "nz"))
-    return 5 if prefilter else 4
+    return 3 if prefilter else 2
+
+
+# scan blocks of the split step compared against the one-stream step (one resident block per SM
+# is 152 on a GB300)
+SPLIT_SCAN_BLOCKS = (8, 38, 152)
+
+
+def split_applies(cfg):
+    """The split step of lbm_step (hydro as two launches, one concurrent with the near-contact pass):
+    3D with the near-contact pass on, nx even and Q N <= 2^32."""
+    n = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    return bool(cfg["nci_on"]) and cfg["dim"] == 3 and cfg["nx"] % 2 == 0 and cfg["Q"] * n <= 2 ** 32
+
+
+def kernels_per_step(cfg, overlap=False):
+    """Kernels one lbm_step launches: the near-contact pass, hydro (two launches in the split step)
+    and phase."""
+    return nci_kernels(cfg) + (2 if overlap and split_applies(cfg) else 1) + 1
 
 
 def step_bytes_per_cell(Q, pop_bytes):
@@ -217,6 +235,7 @@ def run_plan(args, world, rank):
     return {
         "warmup": max(args.warmup, 0), "timed": max(args.steps, 0),
         "split_steps": max(min(args.steps, 500), 1),
+        "split_compare_steps": max(min(args.steps, 500), 1),
         "e2e_steps": max(args.steps, 1) if not args.no_e2e else 0,
         "variant_stores": ("f16", "bf16") if variants else (),
         "variant_timed": max(args.steps, 1), "early": EARLY, "late": LATE,
@@ -275,10 +294,29 @@ def run_ours(args, world, rank, local):
     split = sim.profile_read()
     sim.profile(False)
 
+    # the same steps as the split step (lbm_set_overlap), for comparison: the near-contact pass and
+    # the listed tiles' hydrodynamics on a second stream, concurrent with the other tiles
+    split_step = None
+    if split_applies(cfg) and plan["split_compare_steps"]:
+        ko = plan["split_compare_steps"]
+        split_step = {"unit": "MLUPS", "steps": ko, "one_stream_value": round(mlups / world, 1)}
+        for blocks in SPLIT_SCAN_BLOCKS:
+            sim.set_overlap(blocks)
+            sim.step(3)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(ko)
+            e1.record(stream)
+            e1.synchronize()
+            mo = N * ko / (e0.elapsed_time(e1) * 1e-3) / 1e6
+            split_step[f"scan_blocks_{blocks}"] = {"value": round(mo, 1), "vs_one_stream": round(mo / (mlups / world), 4)}
+        sim.set_overlap(0)
+
     pop_b = 4 if args.store == "f32" else 2
     peak, peak_kind = measured_peaks()
-    hydro_ms, hydro_n = prof["hydro"]
-    hydro_avg = hydro_ms / max(hydro_n, 1)
+    # one hydrodynamic pass per step
+    hydro_ms, _ = prof["hydro"]
+    hydro_avg = hydro_ms / max(plan["timed"], 1)
     per_launch_bytes = hydro_bytes_per_cell(Q, pop_b) * N
     achieved = per_launch_bytes / (hydro_avg * 1e-3) / 1e9
     key = (args.store, Q, _src_hash("hydro_impl.cuh", "lbm_device.cuh"))
@@ -346,14 +384,14 @@ def run_ours(args, world, rank, local):
             mv1, _ = s2.mass()
             s2.close()
             msv = e0.elapsed_time(e1)
-            hm, hn = pr["hydro"]
+            hm, _ = pr["hydro"]
             v_mlups = N * kv / (msv * 1e-3) / 1e6
             d_early = np.abs(fresh(st, plan["early"]) - ph32_early)
             ph_late = fresh(st, plan["late"])
             variants[st] = {
                 "value": round(v_mlups, 1), "steps": kv, "vs_f32": round(v_mlups / mlups, 4),
-                "hydro_gbs": round(hydro_bytes_per_cell(Q, 2) * N / (hm / max(hn, 1) * 1e-3) / 1e9, 1),
-                "hydro_ms": round(hm / max(hn, 1), 5),
+                "hydro_gbs": round(hydro_bytes_per_cell(Q, 2) * N / (hm / kv * 1e-3) / 1e9, 1),
+                "hydro_ms": round(hm / kv, 5),
                 "step_roofline_frac": round(v_mlups * 1e6 * step_bytes_per_cell(Q, 2) / (peak * 1e9), 4),
                 "phi_diff_vs_f32": {
                     f"after_{plan['early']}_steps": {"max": float(d_early.max()),
@@ -401,6 +439,7 @@ def run_ours(args, world, rank, local):
                           "frac_of_8TBs": round(step_frac * peak / 8000.0, 4)},
         "kernels_ms_per_step": {k: round(ms / split_steps, 5) for k, (ms, n) in split.items() if n},
         "kernels_split_steps": split_steps,
+        "split_step": split_step,
         "gpu_launches": gpu_launches,
         "clocks": clocks,
         "e2e": e2e,
@@ -442,7 +481,7 @@ def run_sweep(args, world, rank, local):
         m0.append(s.mass()[0])
         sims.append(s)
     cells = sum(s.N for s in sims)
-    launches_fused = sum(kernels_per_step(c) - 2 for c in cfgs) + 2  # near-contact per case, 2 batched
+    launches_fused = sum(nci_kernels(c) for c in cfgs) + 2  # near-contact per case, 2 batched
     launches_case = sum(kernels_per_step(c) for c in cfgs)
     steps = args.steps + (args.steps & 1)  # whole graph launches
 

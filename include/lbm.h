@@ -109,8 +109,24 @@ int lbm_get_state(lbm_ctx *ctx, double *f, double *phi);
 
 /* Advances n >= 0 steps. Enqueues the work on the context stream and returns; it synchronises
  * only when the periodic mass check runs (mass_check_every > 0), which may return
- * LBM_ERR_UNSTABLE. */
+ * LBM_ERR_UNSTABLE.
+ * A step is the near-contact pass (Sec. 2.3) on phi^n, the hydrodynamic update (Sec. 2.1) and the
+ * phase-field update (Sec. 2.1.1), in that order on the context stream. */
 int lbm_step(lbm_ctx *ctx, int n);
+
+/* The split step of lbm_step, where it applies (3D, nci_on, nx even, Q N <= 2^32): the
+ * near-contact pass and then the hydrodynamic update of the cells of the near-contact tiles listed
+ * for phi^n (32 x 8 x 4 tiles holding a cell with q >= q_th) run on a second, high-priority stream
+ * of the context, while the context stream updates the other cells, which are not gated and so do
+ * not read F_rep (Eq. 73); the streams join before the phase-field update. Each cell is updated by
+ * one of the two launches with the same arithmetic, so every state is bit-identical to the
+ * one-stream step's. blocks > 0 runs it with that many resident near-contact scan blocks (capped
+ * at one per SM); blocks = 0 (the default) runs every step on the context stream alone. Takes
+ * effect at the next lbm_step or batch capture. blocks < 0 or NULL ctx: LBM_ERR_ARG; blocks > 0
+ * on a context where the split step does not apply: LBM_ERR_STATE. */
+int lbm_set_overlap(lbm_ctx *ctx, int blocks);
+/* *blocks = the scan blocks of the split step, 0 when every step runs on one stream. */
+int lbm_get_overlap(const lbm_ctx *ctx, int *blocks);
 
 /* phi^n (N), the velocity u (3N) and p* (N) of the current state: moments of the pre-collision
  * populations with the forces evaluated on phi^n (Eqs. 6-7, with F_nu from u without F_nu).

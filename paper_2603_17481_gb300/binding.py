@@ -68,6 +68,8 @@ def load():
     L.lbm_set_state.argtypes = [_VP, _VP, _VP]
     L.lbm_get_state.argtypes = [_VP, _VP, _VP]
     L.lbm_step.argtypes = [_VP, ctypes.c_int]
+    L.lbm_set_overlap.argtypes = [_VP, ctypes.c_int]
+    L.lbm_get_overlap.argtypes = [_VP, _VP]
     L.lbm_read_fields.argtypes = [_VP, _VP, _VP, _VP]
     L.lbm_mass.argtypes = [_VP, _VP, _VP]
     L.lbm_read_nci.argtypes = [_VP, _VP, _VP]
@@ -92,7 +94,7 @@ def load():
     L.lbm_kernel_name.argtypes = [ctypes.c_int]
     L.lbm_kernel_name.restype = ctypes.c_char_p
     for name in ("lbm_create", "lbm_set_stream", "lbm_init_fields", "lbm_set_state", "lbm_get_state",
-                 "lbm_step", "lbm_read_fields", "lbm_mass", "lbm_mass_noalloc", "lbm_read_nci", "lbm_synchronize",
+                 "lbm_step", "lbm_set_overlap", "lbm_get_overlap", "lbm_read_fields", "lbm_mass", "lbm_mass_noalloc", "lbm_read_nci", "lbm_synchronize",
                  "lbm_profile", "lbm_profile_kinds", "lbm_profile_read", "lbm_lattice", "lbm_batch_create", "lbm_batch_step",
                  "lbm_batch_create_ex", "lbm_batch_config",
                  "lbm_nci_diagnostics", "lbm_curvature", "lbm_energy_spectrum",
@@ -191,6 +193,16 @@ def lbm_get_state(ctx: int, N: int, Q: int):
 
 def lbm_step(ctx: int, n: int) -> None:
     _check(load().lbm_step(_VP(ctx), int(n)), "lbm_step")
+
+
+def lbm_set_overlap(ctx: int, blocks: int) -> None:
+    _check(load().lbm_set_overlap(_VP(ctx), int(blocks)), "lbm_set_overlap")
+
+
+def lbm_get_overlap(ctx: int) -> int:
+    b = ctypes.c_int(0)
+    _check(load().lbm_get_overlap(_VP(ctx), ctypes.byref(b)), "lbm_get_overlap")
+    return b.value
 
 
 def lbm_read_fields(ctx: int, N: int, phi=None, u=None, pstar=None, want=("phi", "u", "pstar")):
@@ -397,6 +409,12 @@ class Lbm:
 
     def step(self, n: int = 1):
         lbm_step(self.ctx, n)
+
+    def set_overlap(self, blocks: int):
+        lbm_set_overlap(self.ctx, blocks)
+
+    def overlap(self) -> int:
+        return lbm_get_overlap(self.ctx)
 
     def read_fields(self, **kw):
         return lbm_read_fields(self.ctx, self.N, **kw)

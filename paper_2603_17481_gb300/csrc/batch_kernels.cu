@@ -38,7 +38,6 @@ k_hydro2_batch(const BatchCase *__restrict__ cases, const int4 *__restrict__ ite
     fetch(it + gridDim.x, buf ^ 1);  // in flight during this item
     const BatchCase &C = *reinterpret_cast<const BatchCase *>(s_case[buf]);
     const int4 w = s_item[buf];
-    if ((w.y | w.z | w.w) == 0 && C.reset && tid == 0) *C.reset = 0;
     hydro2_tile<L, S, kStep, TY, TZ>(C.P, (const T *)C.src, (T *)C.dst, C.phi, C.frep, C.u, nullptr, w.y, w.z, w.w);
     __syncthreads();  // this item's staged phi and case record are no longer read
     buf ^= 1;
@@ -49,6 +48,8 @@ template <int M>
 __global__ void __launch_bounds__(March3::NT, LBM_MARCH_MINB)
 k_phase3m_batch(const BatchCase *__restrict__ cases, const long long *__restrict__ uoff, const int ncases) {
   pdl_enter();
+  // the marks of the lists of phi^n: block b clears those of cases b, b + grid, ...
+  for (int c = blockIdx.x; c < ncases; c += gridDim.x) clear_marks(cases[c].prev, threadIdx.x, March3::NT);
   const long long units = uoff[ncases];
   const long long nwarps = (long long)gridDim.x * March3::WARPS;
   const long long wid = (long long)blockIdx.x * March3::WARPS + (threadIdx.x >> 5);
@@ -74,7 +75,7 @@ k_phase3m_batch(const BatchCase *__restrict__ cases, const long long *__restrict
     const long long end = min(ue, uoff[c + 1]);
     const int z1 = (int)min((long long)nz, (long long)z0 + (end - ub));
     ub += z1 - z0;
-    march_run<M>(C.P, C.phi, C.u, C.phi_out, C.tiles, C.ntiles, C.lflag, C.ncx, col, z0, z1);
+    march_run<M>(C.P, C.phi, C.u, C.phi_out, C.next.tiles, C.next.count, C.next.mark, C.ncx, col, z0, z1);
   }
 }
 

@@ -31,9 +31,16 @@ struct lbm_ctx {
   int32_t *partner = nullptr;
   int *tiles[2] = {nullptr, nullptr};
   int *ntiles = nullptr;  // 2 counters, one per phi buffer
-  int *lflag = nullptr;   // per near-contact tile: listed by the running phase pass (3D)
+  int *lflag = nullptr;   // 2 x ntile marks: tile listed for phi[k] (3D)
+  int ntile = 0;          // near-contact tiles of the grid
   lbm::NciAux aux;        // near-contact prefilter buffers (3D grids with sides multiple of 4)
   int nci_blocks = 0;
+  // the split step: the near-contact pass and the hydrodynamic update of the listed tiles on the
+  // high-priority stream `side`, concurrent with the hydrodynamic update of the other tiles
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int overlap_blocks = 0;  // resident near-contact scan blocks while split; 0: one stream
+  int split_blocks = 0;    // blocks of the listed-tile hydrodynamic launch
   lbm::ReduceOut *red_part = nullptr, *red_out = nullptr;
   lbm::DiagOut *diag_part = nullptr, *diag_out = nullptr;  // film statistics, on first use
   unsigned long long *curv_hist = nullptr;  // curvature histogram (kMaxCurvBins), on first use
@@ -52,10 +59,23 @@ struct lbm_ctx {
   int64_t prof_n[LBM_K_COUNT] = {0};
 };
 
+// The near-contact list of phi buffer k.
+inline lbm::TileList tile_list(const lbm_ctx *c, int k) {
+  lbm::TileList t;
+  t.tiles = c->tiles[k];
+  t.count = c->ntiles + k;
+  t.mark = c->lflag + (size_t)k * (size_t)c->ntile;
+  return t;
+}
+
 // The prefilter buffers of the near-contact pass over listed tiles, or nullptr where it does not apply.
 inline const lbm::NciAux *nci_aux(const lbm_ctx *c) { return c->aux.bricks ? &c->aux : nullptr; }
 // Kernels of one near-contact pass over the listed tiles: normals, prefilter (where it applies), scan.
 inline int nci_list_kernels(const lbm_ctx *c) { return nci_aux(c) ? 3 : 2; }
+
+// Enqueues one step of c on stream s from buffers (cur, pcur) (lbm_api.cu); lists = false leaves the
+// near-contact lists as they are. Returns an lbm_status.
+int enqueue_step(lbm_ctx *c, int cur, int pcur, bool lists, cudaStream_t s);
 
 // Looks up (once per device, current device) the static scratch of lbm_mass_noalloc, which loads
 // its module; lbm_create calls it. Returns an lbm_status.

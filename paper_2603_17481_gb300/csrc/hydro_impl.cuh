@@ -342,7 +342,7 @@ template <class L, int S, int MODE, bool I32>
 __global__ void __launch_bounds__(Tile<L::D>::X * Tile<L::D>::Y * Tile<L::D>::Z, L::Q >= 27 ? 4 : LBM_HYDRO_MINB)
 k_hydro(const KParams P, const typename Store<S>::T *__restrict__ src, typename Store<S>::T *__restrict__ dst,
         const int32_t *__restrict__ phi, const float4 *__restrict__ frep, float *__restrict__ u_out,
-        float *__restrict__ ps_out, int *__restrict__ reset) {
+        float *__restrict__ ps_out) {
   pdl_enter();
   constexpr int DIM = L::D;
   using SL = typename StencilOf<DIM>::type;
@@ -355,8 +355,6 @@ k_hydro(const KParams P, const typename Store<S>::T *__restrict__ src, typename 
   const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
   const int nx = P.nx, ny = P.ny, nz = P.nz;
   const int x0 = blockIdx.x * TT::X, y0 = blockIdx.y * TT::Y, z0 = blockIdx.z * TT::Z;
-  // the near-contact tile list of this phi has been consumed: clear its count for reuse
-  if (reset && (blockIdx.x | blockIdx.y | blockIdx.z | tx | ty | tz) == 0) *reset = 0;
 
   // stage phi (tile + 1 halo): warp w loads rows w, w + NWARPS, ...
   {
@@ -486,11 +484,14 @@ template <int TY, int TZ> struct Hydro2Smem {
 
 // One tile (bx, by, bz) of 64 x TY x TZ cells with a block of 32 x TY x TZ threads. Every thread
 // of the block calls it (one barrier inside; a caller looping over tiles adds one between tiles).
+// halves: bit 0 updates the cells x0 .. x0 + 31 (lanes 0 - 15), bit 1 x0 + 32 .. x0 + 63; the
+// lanes of a half that is not updated still pull (their neighbours' shifted pairs need them).
 template <class L, int S, int MODE, int TY, int TZ>
 __device__ __forceinline__ void hydro2_tile(const KParams &P, const typename Store<S>::T *__restrict__ src,
                                             typename Store<S>::T *__restrict__ dst, const int32_t *__restrict__ phi,
                                             const float4 *__restrict__ frep, float *__restrict__ u_out,
-                                            float *__restrict__ ps_out, const int bx, const int by, const int bz) {
+                                            float *__restrict__ ps_out, const int bx, const int by, const int bz,
+                                            const unsigned halves = 3u) {
   __shared__ __align__(16) float s_phi[Hydro2Smem<TY, TZ>::FLOATS];
   static_assert(L::D == 3, "3D lattices");
   using SL = D3Q27;
@@ -569,7 +570,7 @@ __device__ __forceinline__ void hydro2_tile(const KParams &P, const typename Sto
   }
   __syncthreads();
   if constexpr (S == 0) pull();
-  if (!in) return;  // no barrier follows
+  if (!in || !((halves >> (lane >> 4)) & 1u)) return;  // no barrier or shuffle follows
 
   // isotropic gradient and Laplacian of phi (Eqs. 22-23) at both cells: columns x - 1 .. x + 2 of
   // the nine stencil rows as two 8-byte shared loads each
@@ -627,19 +628,62 @@ __device__ __forceinline__ void hydro2_tile(const KParams &P, const typename Sto
   if constexpr (MODE == kMoments) *reinterpret_cast<float2 *>(ps_out + idx) = pso.v;
 }
 
+// The near-contact tiles (32 x 8 x 4) holding the two halves of the paired tile (bx, by, bz) of
+// 64 x 4 x 2 cells: tiles 2 bx and 2 bx + 1 of the row (by / 2, bz / 2); the second is -1 beyond
+// the grid.
+static_assert(NciTile<3>::X == 32 && NciTile<3>::Y == 8 && NciTile<3>::Z == 4,
+              "a near-contact tile holds 2 x 2 paired tiles of 64 x 4 x 2 cells in y, z, and half of one in x");
+__device__ __forceinline__ int2 nci_tiles_of_pair(const KParams &P, int bx, int by, int bz) {
+  const int gtx = (P.nx + 31) >> 5, gty = (P.ny + 7) >> 3;
+  const int t0 = 2 * bx + gtx * ((by >> 1) + gty * (bz >> 1));
+  return make_int2(t0, 2 * bx + 1 < gtx ? t0 + 1 : -1);
+}
+
+// listed == nullptr: every cell. Otherwise the split step's first part: only the halves whose
+// near-contact tile is not listed (a block with both halves listed returns at once).
 template <class L, int S, int MODE>
 __global__ void __launch_bounds__(256, L::Q >= 27 ? 2 : LBM_HYDRO2_MINB)
 k_hydro2(const KParams P, const typename Store<S>::T *__restrict__ src, typename Store<S>::T *__restrict__ dst,
          const int32_t *__restrict__ phi, const float4 *__restrict__ frep, float *__restrict__ u_out,
-         float *__restrict__ ps_out, int *__restrict__ reset) {
+         float *__restrict__ ps_out, const int *__restrict__ listed) {
   pdl_enter();
-  if (reset && (blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y | threadIdx.z) == 0) *reset = 0;
-  hydro2_tile<L, S, MODE, 4, 2>(P, src, dst, phi, frep, u_out, ps_out, blockIdx.x, blockIdx.y, blockIdx.z);
+  unsigned halves = 3u;
+  if (listed) {
+    const int2 t = nci_tiles_of_pair(P, blockIdx.x, blockIdx.y, blockIdx.z);
+    halves = (listed[t.x] ? 0u : 1u) | (t.y >= 0 && listed[t.y] ? 0u : 2u);
+    if (halves == 0u) return;  // block-uniform
+  }
+  hydro2_tile<L, S, MODE, 4, 2>(P, src, dst, phi, frep, u_out, ps_out, blockIdx.x, blockIdx.y, blockIdx.z, halves);
+}
+
+// The split step's second part: the cells of the listed near-contact tiles. Item i of 4 n covers
+// the paired tile (tx / 2, 2 ty + (i & 1), 2 tz + (i >> 1 & 1)) of listed tile i / 4 = (tx, ty, tz);
+// when both near-contact tiles of a pair are listed, the even one's items update both halves and
+// the odd one's items are skipped, so every cell is written once.
+template <class L, int S>
+__global__ void __launch_bounds__(256, L::Q >= 27 ? 2 : LBM_HYDRO2_MINB)
+k_hydro2_listed(const KParams P, const typename Store<S>::T *__restrict__ src, typename Store<S>::T *__restrict__ dst,
+                const int32_t *__restrict__ phi, const float4 *__restrict__ frep, float *__restrict__ u_out,
+                const int *__restrict__ tiles, const int *__restrict__ ntiles, const int *__restrict__ listed) {
+  pdl_enter();
+  const int n4 = 4 * *ntiles;
+  const int gtx = (P.nx + 31) >> 5, gty = (P.ny + 7) >> 3;
+  for (int it = blockIdx.x; it < n4; it += gridDim.x) {
+    const int tile = tiles[it >> 2];
+    const int tx = tile % gtx, tyz = tile / gtx;
+    const int ty = tyz % gty, tz = tyz / gty;
+    if ((tx & 1) && listed[tile - 1]) continue;  // block-uniform: the even tile's items cover it
+    const int bx = tx >> 1, by = 2 * ty + (it & 1), bz = 2 * tz + ((it >> 1) & 1);
+    if (4 * by >= P.ny || 2 * bz >= P.nz) continue;
+    const unsigned halves = (tx & 1) ? 2u : (1u | (tx + 1 < gtx && listed[tile + 1] ? 2u : 0u));
+    hydro2_tile<L, S, kStep, 4, 2>(P, src, dst, phi, frep, u_out, nullptr, bx, by, bz, halves);
+    __syncthreads();  // the staged phi of this item is no longer read
+  }
 }
 
 template <class L, int S>
 cudaError_t launch_hydro_t(int mode, const KParams &P, const void *src, void *dst, const int32_t *phi,
-                           const float4 *frep, float *u, float *pstar, int *reset, cudaStream_t s) {
+                           const float4 *frep, float *u, float *pstar, cudaStream_t s) {
   using TT = Tile<L::D>;
   using T = typename Store<S>::T;
   dim3 block(TT::X, TT::Y, TT::Z);
@@ -647,28 +691,54 @@ cudaError_t launch_hydro_t(int mode, const KParams &P, const void *src, void *ds
   const bool i32 = (long long)L::Q * P.N <= (1LL << 32);  // largest offset Q N - 1 fits an unsigned
   const T *a = (const T *)src;
   T *b = (T *)dst;
+  const int *all = nullptr;
   if constexpr (L::D == 3) {
     if (i32 && P.nx % 2 == 0) {
       dim3 g2((P.nx + 63) / 64, (P.ny + 3) / 4, (P.nz + 1) / 2);
-      return mode == kStep ? launch_pdl(k_hydro2<L, S, kStep>, g2, block, 0, s, P, a, b, phi, frep, u, pstar, reset)
-                           : launch_pdl(k_hydro2<L, S, kMoments>, g2, block, 0, s, P, a, b, phi, frep, u, pstar, reset);
+      return mode == kStep ? launch_pdl(k_hydro2<L, S, kStep>, g2, block, 0, s, P, a, b, phi, frep, u, pstar, all)
+                           : launch_pdl(k_hydro2<L, S, kMoments>, g2, block, 0, s, P, a, b, phi, frep, u, pstar, all);
     }
   }
   if (mode == kStep)
-    return i32 ? launch_pdl(k_hydro<L, S, kStep, true>, grid, block, 0, s, P, a, b, phi, frep, u, pstar, reset)
-               : launch_pdl(k_hydro<L, S, kStep, false>, grid, block, 0, s, P, a, b, phi, frep, u, pstar, reset);
-  return i32 ? launch_pdl(k_hydro<L, S, kMoments, true>, grid, block, 0, s, P, a, b, phi, frep, u, pstar, reset)
-             : launch_pdl(k_hydro<L, S, kMoments, false>, grid, block, 0, s, P, a, b, phi, frep, u, pstar, reset);
+    return i32 ? launch_pdl(k_hydro<L, S, kStep, true>, grid, block, 0, s, P, a, b, phi, frep, u, pstar)
+               : launch_pdl(k_hydro<L, S, kStep, false>, grid, block, 0, s, P, a, b, phi, frep, u, pstar);
+  return i32 ? launch_pdl(k_hydro<L, S, kMoments, true>, grid, block, 0, s, P, a, b, phi, frep, u, pstar)
+             : launch_pdl(k_hydro<L, S, kMoments, false>, grid, block, 0, s, P, a, b, phi, frep, u, pstar);
 }
 
 template <class L>
 cudaError_t launch_hydro_lattice(int store, int mode, const KParams &P, const void *src, void *dst,
-                                 const int32_t *phi, const float4 *frep, float *u, float *pstar, int *reset,
-                                 cudaStream_t s) {
+                                 const int32_t *phi, const float4 *frep, float *u, float *pstar, cudaStream_t s) {
   switch (store) {
-    case 0: return launch_hydro_t<L, 0>(mode, P, src, dst, phi, frep, u, pstar, reset, s);
-    case 1: return launch_hydro_t<L, 1>(mode, P, src, dst, phi, frep, u, pstar, reset, s);
-    default: return launch_hydro_t<L, 2>(mode, P, src, dst, phi, frep, u, pstar, reset, s);
+    case 0: return launch_hydro_t<L, 0>(mode, P, src, dst, phi, frep, u, pstar, s);
+    case 1: return launch_hydro_t<L, 1>(mode, P, src, dst, phi, frep, u, pstar, s);
+    default: return launch_hydro_t<L, 2>(mode, P, src, dst, phi, frep, u, pstar, s);
+  }
+}
+
+template <class L, int S>
+cudaError_t launch_split_t(int part, const KParams &P, const void *src, void *dst, const int32_t *phi,
+                           const float4 *frep, float *u, const TileList &listed, int blocks, cudaStream_t s) {
+  using T = typename Store<S>::T;
+  const T *a = (const T *)src;
+  T *b = (T *)dst;
+  if (part == 0) {
+    dim3 g2((P.nx + 63) / 64, (P.ny + 3) / 4, (P.nz + 1) / 2);
+    return launch_pdl(k_hydro2<L, S, kStep>, g2, dim3(32, 4, 2), 0, s, P, a, b, phi, frep, u, (float *)nullptr,
+                      (const int *)listed.mark);
+  }
+  return launch_pdl(k_hydro2_listed<L, S>, dim3(blocks > 0 ? blocks : 1), dim3(32, 4, 2), 0, s, P, a, b, phi, frep,
+                    u, (const int *)listed.tiles, (const int *)listed.count, (const int *)listed.mark);
+}
+
+template <class L>
+cudaError_t launch_split_lattice(int part, int store, const KParams &P, const void *src, void *dst,
+                                 const int32_t *phi, const float4 *frep, float *u, const TileList &listed,
+                                 int blocks, cudaStream_t s) {
+  switch (store) {
+    case 0: return launch_split_t<L, 0>(part, P, src, dst, phi, frep, u, listed, blocks, s);
+    case 1: return launch_split_t<L, 1>(part, P, src, dst, phi, frep, u, listed, blocks, s);
+    default: return launch_split_t<L, 2>(part, P, src, dst, phi, frep, u, listed, blocks, s);
   }
 }
 

@@ -5,9 +5,8 @@
 namespace lbm {
 
 cudaError_t launch_hydro_q9(int store, int mode, const KParams &P, const void *src, void *dst,
-                             const int32_t *phi, const float4 *frep, float *u, float *pstar, int *reset,
-                             cudaStream_t s) {
-  return launch_hydro_lattice<D2Q9>(store, mode, P, src, dst, phi, frep, u, pstar, reset, s);
+                             const int32_t *phi, const float4 *frep, float *u, float *pstar, cudaStream_t s) {
+  return launch_hydro_lattice<D2Q9>(store, mode, P, src, dst, phi, frep, u, pstar, s);
 }
 
 }  // namespace lbm

@@ -5,20 +5,35 @@
 namespace lbm {
 
 cudaError_t launch_hydro_q9(int, int, const KParams &, const void *, void *, const int32_t *, const float4 *,
-                            float *, float *, int *, cudaStream_t);
+                            float *, float *, cudaStream_t);
 cudaError_t launch_hydro_q19(int, int, const KParams &, const void *, void *, const int32_t *, const float4 *,
-                             float *, float *, int *, cudaStream_t);
+                             float *, float *, cudaStream_t);
 cudaError_t launch_hydro_q27(int, int, const KParams &, const void *, void *, const int32_t *, const float4 *,
-                             float *, float *, int *, cudaStream_t);
+                             float *, float *, cudaStream_t);
+cudaError_t launch_split_q19(int, int, const KParams &, const void *, void *, const int32_t *, const float4 *,
+                             float *, const TileList &, int, cudaStream_t);
+cudaError_t launch_split_q27(int, int, const KParams &, const void *, void *, const int32_t *, const float4 *,
+                             float *, const TileList &, int, cudaStream_t);
 
 cudaError_t launch_hydro(int Q, int store, int mode, const KParams &P, const void *src, void *dst,
-                         const int32_t *phi, const float4 *frep, float *u, float *pstar, int *reset,
-                         cudaStream_t s) {
+                         const int32_t *phi, const float4 *frep, float *u, float *pstar, cudaStream_t s) {
   switch (Q) {
-    case 9: return launch_hydro_q9(store, mode, P, src, dst, phi, frep, u, pstar, reset, s);
-    case 19: return launch_hydro_q19(store, mode, P, src, dst, phi, frep, u, pstar, reset, s);
-    default: return launch_hydro_q27(store, mode, P, src, dst, phi, frep, u, pstar, reset, s);
+    case 9: return launch_hydro_q9(store, mode, P, src, dst, phi, frep, u, pstar, s);
+    case 19: return launch_hydro_q19(store, mode, P, src, dst, phi, frep, u, pstar, s);
+    default: return launch_hydro_q27(store, mode, P, src, dst, phi, frep, u, pstar, s);
   }
+}
+
+bool hydro_split_applies(int Q, const KParams &P) {
+  return (Q == 19 || Q == 27) && P.nx % 2 == 0 && (long long)Q * P.N <= (1LL << 32);
+}
+
+cudaError_t launch_hydro_split(int part, int Q, int store, const KParams &P, const void *src, void *dst,
+                               const int32_t *phi, const float4 *frep, float *u, const TileList &listed, int blocks,
+                               cudaStream_t s) {
+  if (!hydro_split_applies(Q, P)) return cudaErrorInvalidValue;
+  return Q == 19 ? launch_split_q19(part, store, P, src, dst, phi, frep, u, listed, blocks, s)
+                 : launch_split_q27(part, store, P, src, dst, phi, frep, u, listed, blocks, s);
 }
 
 int tile_count(int dim, const KParams &P) {

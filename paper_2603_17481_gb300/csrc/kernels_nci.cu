@@ -82,8 +82,10 @@ __device__ __forceinline__ void tile_of(int tile, int gtx, int gty, int &bx, int
 // Normals of the gated cells of the listed tiles (or of every tile when tiles == nullptr), 2D.
 __global__ void __launch_bounds__(NciGeom<2>::NT)
 k_nci_normals2(const KParams P, const int32_t *__restrict__ phi, float4 *__restrict__ nrm,
-               const int *__restrict__ tiles, const int *__restrict__ ntiles, int total, int gtx, int gty) {
+               const int *__restrict__ tiles, const int *__restrict__ ntiles, int total, int gtx, int gty,
+               int *__restrict__ reset_other) {
   pdl_enter();
+  if (reset_other && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) *reset_other = 0;
   using G = NciGeom<2>;
   using SL = StencilOf<2>::type;
   const int n = tiles ? *ntiles : total;
@@ -129,8 +131,9 @@ struct NrmBox {
 __global__ void __launch_bounds__(kNrmThreads)
 k_nci_normals3(const KParams P, const int32_t *__restrict__ phi, float4 *__restrict__ nrm, float4 *__restrict__ frep,
                const int *__restrict__ tiles, const int *__restrict__ ntiles, int total, int gtx, int gty,
-               const NciAux aux, int *__restrict__ lflag) {
+               const NciAux aux, int *__restrict__ reset_other) {
   pdl_enter();
+  if (reset_other && blockIdx.x == 0 && threadIdx.x == 0) *reset_other = 0;
   using G = NciGeom<3>;
   using SL = StencilOf<3>::type;
   using B = NrmBox;
@@ -149,7 +152,6 @@ k_nci_normals3(const KParams P, const int32_t *__restrict__ phi, float4 *__restr
     int bx, by, bz;
     tile_of<3>(tile, gtx, gty, bx, by, bz);
     if (bricks && half == 0 && threadIdx.x == 0) aux.flags[tile] = 1;
-    if (lflag && tiles && half == 0 && threadIdx.x == 0) lflag[tile] = 0;  // the phase kernel's mark
     const int x0 = bx * G::TX, y0 = by * G::TY + 4 * half, z0 = bz * G::TZ;
     {
       const int xa = wrapn(x0 - 1 + lane, nx), xb = wrapn(x0 + 31 + (lane & 1), nx);
@@ -669,7 +671,7 @@ static cudaError_t nci_attr() {
 template <int DIM>
 static cudaError_t launch_nci_dim(const KParams &P, const NciTable &T, const int32_t *phi, float4 *nrm, float4 *frep,
                                   int32_t *partner, int debug, const int *tiles, const int *ntiles, int list_blocks,
-                                  cudaStream_t s, const NciAux *aux, int *lflag) {
+                                  cudaStream_t s, const NciAux *aux, int *reset_other) {
   using G = NciGeom<DIM>;
   cudaError_t e = nci_attr<DIM>();
   if (e != cudaSuccess) return e;
@@ -680,13 +682,14 @@ static cudaError_t launch_nci_dim(const KParams &P, const NciTable &T, const int
   const bool pre = DIM == 3 && aux && tiles && aux->bricks && nci_aux_applies(DIM, P);
   const NciAux none{};
   if constexpr (DIM == 2) {
-    cudaError_t e2 = launch_pdl(k_nci_normals2, dim3(blocks), block, 0, s, P, phi, nrm, tiles, ntiles, total, gtx, gty);
+    cudaError_t e2 = launch_pdl(k_nci_normals2, dim3(blocks), block, 0, s, P, phi, nrm, tiles, ntiles, total, gtx, gty,
+                                tiles ? reset_other : nullptr);
     if (e2 != cudaSuccess) return e2;
   } else {
     // one block per half tile, at most 16 blocks per resident scan block (grid-stride beyond)
     const int nb = 2 * total < 16 * list_blocks ? 2 * total : 16 * list_blocks;
     cudaError_t e3 = launch_pdl(k_nci_normals3, dim3(nb), dim3(kNrmThreads), 0, s, P, phi, nrm, frep, tiles, ntiles, total,
-                                gtx, gty, pre ? *aux : none, tiles ? lflag : nullptr);
+                                gtx, gty, pre ? *aux : none, tiles ? reset_other : nullptr);
     if (e3 != cudaSuccess) return e3;
   }
   if (!pre) {
@@ -702,9 +705,11 @@ static cudaError_t launch_nci_dim(const KParams &P, const NciTable &T, const int
 
 cudaError_t launch_nci(int dim, const KParams &P, const NciTable &T, const int32_t *phi, float4 *nrm, float4 *frep,
                        int32_t *partner, int debug, const int *tiles, const int *ntiles, int list_blocks,
-                       cudaStream_t s, const NciAux *aux, int *lflag) {
-  return dim == 2 ? launch_nci_dim<2>(P, T, phi, nrm, frep, partner, debug, tiles, ntiles, list_blocks, s, aux, lflag)
-                  : launch_nci_dim<3>(P, T, phi, nrm, frep, partner, debug, tiles, ntiles, list_blocks, s, aux, lflag);
+                       cudaStream_t s, const NciAux *aux, int *reset_other) {
+  return dim == 2 ? launch_nci_dim<2>(P, T, phi, nrm, frep, partner, debug, tiles, ntiles, list_blocks, s, aux,
+                                      reset_other)
+                  : launch_nci_dim<3>(P, T, phi, nrm, frep, partner, debug, tiles, ntiles, list_blocks, s, aux,
+                                      reset_other);
 }
 
 bool nci_aux_applies(int dim, const KParams &P) {

@@ -260,8 +260,8 @@ cudaError_t phase_prepare(int dim) {
   return e;
 }
 
-static cudaError_t launch_phase3(const KParams &P, const int32_t *phi, const float *u, int32_t *phi_out, int *tiles,
-                                 int *ntiles, int *lflag, cudaStream_t s) {
+static cudaError_t launch_phase3(const KParams &P, const int32_t *phi, const float *u, int32_t *phi_out,
+                                 const TileList &next, const TileList &prev, cudaStream_t s) {
   const cudaError_t e = phase_prepare(3);
   if (e != cudaSuccess) return e;
   // one resident wave of warps sharing the (column, plane) units equally, at least MIN_RUN planes each
@@ -272,20 +272,22 @@ static cudaError_t launch_phase3(const KParams &P, const int32_t *phi, const flo
   long long blocks = (want + March3::WARPS - 1) / March3::WARPS;
   if (blocks > g_march_slots) blocks = g_march_slots;
   if (blocks < 1) blocks = 1;
-  return launch_pdl(k_phase3m<M>, dim3((unsigned)blocks), dim3(March3::NT), 0, s, P, phi, u, phi_out, tiles, ntiles,
-                    lflag, ncx, units);
+  const TileList none{};
+  return launch_pdl(k_phase3m<M>, dim3((unsigned)blocks), dim3(March3::NT), 0, s, P, phi, u, phi_out,
+                    next.tiles ? next : none, next.tiles ? prev : none, ncx, units);
 }
 
 cudaError_t launch_phase(int dim, const KParams &P, const int32_t *phi, const float *u, int32_t *phi_out,
-                         int *tiles, int *ntiles, int *lflag, cudaStream_t s) {
-  return dim == 2 ? launch_phase_dim<2>(P, phi, u, phi_out, tiles, ntiles, s)
-                  : launch_phase3(P, phi, u, phi_out, tiles, ntiles, lflag, s);
+                         const TileList &next, const TileList &prev, cudaStream_t s) {
+  return dim == 2 ? launch_phase_dim<2>(P, phi, u, phi_out, next.tiles, next.count, s)
+                  : launch_phase3(P, phi, u, phi_out, next, prev, s);
 }
 
 // Lists the tiles holding an interfacial cell of phi (used after the state is set from the host).
 template <int DIM>
 __global__ void __launch_bounds__(PhaseGeom<DIM>::NT)
-k_gate_tiles(const KParams P, const int32_t *__restrict__ phi, int *__restrict__ tiles, int *__restrict__ ntiles) {
+k_gate_tiles(const KParams P, const int32_t *__restrict__ phi, int *__restrict__ tiles, int *__restrict__ ntiles,
+             int *__restrict__ mark) {
   using G = PhaseGeom<DIM>;
   const int x = blockIdx.x * G::TX + threadIdx.x, y = blockIdx.y * G::TY + threadIdx.y,
             z = blockIdx.z * G::TZ + threadIdx.z;
@@ -293,19 +295,22 @@ k_gate_tiles(const KParams P, const int32_t *__restrict__ phi, int *__restrict__
   if (x < P.nx && y < P.ny && z < P.nz)
     gated = q_gate_value(phi[(long long)x + (long long)P.nx * (y + (long long)P.ny * z)]) >= P.q_th;
   const int any = __syncthreads_or(gated);
-  if (any && threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0)
-    tiles[atomicAdd(ntiles, 1)] = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  if (any && threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) {
+    const int tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    tiles[atomicAdd(ntiles, 1)] = tile;
+    if (mark) mark[tile] = 1;
+  }
 }
 
-cudaError_t launch_gate_tiles(int dim, const KParams &P, const int32_t *phi, int *tiles, int *ntiles, cudaStream_t s) {
+cudaError_t launch_gate_tiles(int dim, const KParams &P, const int32_t *phi, const TileList &list, cudaStream_t s) {
   if (dim == 2) {
     using G = PhaseGeom<2>;
     dim3 grid((P.nx + G::TX - 1) / G::TX, (P.ny + G::TY - 1) / G::TY, 1);
-    k_gate_tiles<2><<<grid, dim3(G::TX, G::TY, G::TZ), 0, s>>>(P, phi, tiles, ntiles);
+    k_gate_tiles<2><<<grid, dim3(G::TX, G::TY, G::TZ), 0, s>>>(P, phi, list.tiles, list.count, nullptr);
   } else {
     using G = PhaseGeom<3>;
     dim3 grid((P.nx + G::TX - 1) / G::TX, (P.ny + G::TY - 1) / G::TY, (P.nz + G::TZ - 1) / G::TZ);
-    k_gate_tiles<3><<<grid, dim3(G::TX, G::TY, G::TZ), 0, s>>>(P, phi, tiles, ntiles);
+    k_gate_tiles<3><<<grid, dim3(G::TX, G::TY, G::TZ), 0, s>>>(P, phi, list.tiles, list.count, list.mark);
   }
   return cudaGetLastError();
 }

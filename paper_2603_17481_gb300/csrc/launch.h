@@ -50,25 +50,48 @@ size_t nci_brick_count(const KParams &P);
 // otherwise only the ntiles listed tiles, walked by list_blocks resident blocks. With aux (listed
 // tiles only), the normals pass also writes zero force at every gated cell and the brick ranges,
 // a prefilter keeps the tiles whose bricks may face another interface, and only those are scanned.
-// lflag (3D, listed tiles): the phase kernel's marks of the listed tiles, cleared here.
+// reset_other (listed tiles, may be null): the count of the other phi buffer's list, whose tiles
+// were consumed by the previous step; the normals pass sets it to zero, so that the phase pass of
+// this step starts that buffer's list empty.
 cudaError_t launch_nci(int dim, const KParams &P, const NciTable &T, const int32_t *phi, float4 *nrm, float4 *frep,
                        int32_t *partner, int debug, const int *tiles, const int *ntiles, int list_blocks,
-                       cudaStream_t s, const NciAux *aux = nullptr, int *lflag = nullptr);
+                       cudaStream_t s, const NciAux *aux = nullptr, int *reset_other = nullptr);
 int nci_list_blocks(int dim);
 cudaError_t phase_prepare(int dim);
 
 // src/dst are population buffers of the store type; MODE kStep writes dst and u, kMoments writes
 // u and pstar only.
 cudaError_t launch_hydro(int Q, int store, int mode, const KParams &P, const void *src, void *dst,
-                         const int32_t *phi, const float4 *frep, float *u, float *pstar, int *reset,
-                         cudaStream_t s);
+                         const int32_t *phi, const float4 *frep, float *u, float *pstar, cudaStream_t s);
 
-// Also appends to tiles/ntiles (if not null) the tiles of phi_out that hold an interfacial cell.
-// lflag (one int per near-contact tile, all zero on entry) marks the tiles already appended in 3D;
-// the near-contact normals pass that consumes the list clears the marks of its tiles.
+// The near-contact list of one phi buffer: the 32 x 8 x 4 tiles (3D; 32 x 8 in 2D) holding a
+// gated cell, their count, and one mark per tile of the grid (3D), set while the tile is listed.
+struct TileList {
+  int *tiles = nullptr;
+  int *count = nullptr;
+  int *mark = nullptr;
+};
+
+// The hydrodynamic step split in two launches around the near-contact pass (3D, nx even,
+// Q N <= 2^32: the paired kernel). part 0 updates every 64 x 4 x 2 tile half whose near-contact
+// tile is not marked in `listed` (those cells are not gated, so they never read frep, and it may
+// run while the near-contact pass writes frep); part 1 walks the listed tiles on `blocks`
+// resident blocks and updates the rest, after the near-contact pass. Each cell is written by
+// exactly one part, with the arithmetic of launch_hydro.
+bool hydro_split_applies(int Q, const KParams &P);
+cudaError_t launch_hydro_split(int part, int Q, int store, const KParams &P, const void *src, void *dst,
+                               const int32_t *phi, const float4 *frep, float *u, const TileList &listed, int blocks,
+                               cudaStream_t s);
+
+// Also builds `next` (if its tiles are not null): appends the tiles of phi_out that hold an
+// interfacial cell, using next.mark (all zero on entry) in 3D so that each is appended once.
+// In 3D the marks of `prev` (the list of phi, consumed by this step's near-contact and
+// hydrodynamic passes) are cleared, so that buffer's marks are zero when its list is built again.
 cudaError_t launch_phase(int dim, const KParams &P, const int32_t *phi, const float *u, int32_t *phi_out,
-                         int *tiles, int *ntiles, int *lflag, cudaStream_t s);
-cudaError_t launch_gate_tiles(int dim, const KParams &P, const int32_t *phi, int *tiles, int *ntiles, cudaStream_t s);
+                         const TileList &next, const TileList &prev, cudaStream_t s);
+// Lists (and in 3D marks) the tiles holding an interfacial cell of phi (after the state is set
+// from the host); the count and the marks are zero on entry.
+cudaError_t launch_gate_tiles(int dim, const KParams &P, const int32_t *phi, const TileList &list, cudaStream_t s);
 int tile_count(int dim, const KParams &P);
 
 // Geometry of the 3D phase-field register march (phase3_march.cuh).
@@ -89,11 +112,9 @@ struct __align__(16) BatchCase {
   int32_t *phi_out;     // phi^{n+1}
   const float4 *frep;   // near-contact force at the gated cells of phi^n
   float *u;             // velocity, written by the hydrodynamic pass, read by the phase pass
-  int *reset;           // count of the near-contact list of phi^n (cleared by hydro), or null
-  int *tiles, *ntiles;  // near-contact list of phi^{n+1} (appended by the phase pass), or null
-  int *lflag;           // marks of the listed tiles
+  TileList next;        // near-contact list of phi^{n+1}, built by the phase pass (tiles null: none)
+  TileList prev;        // near-contact list of phi^n, whose marks the phase pass clears
   int ncx;              // x segments of the phase march
-  int pad;
 };
 // The paired hydrodynamic kernel over a list of (case, bx, by, bz) tile items of 64 x ty x tz cells
 // (ty x tz = 8; all cases D3Q19 or D3Q27 per Q, one store type, nx even, Q N <= 2^32), on a grid of

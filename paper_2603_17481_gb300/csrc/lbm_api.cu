@@ -10,7 +10,7 @@
 //   mom      4*N float    u and p* of lbm_read_fields / lbm_mass (allocated on first use)
 //   stage    k*N double   FP64 staging of host I/O (allocated on first use, grown as needed)
 //   tiles[2] int          near-contact tiles holding an interfacial cell of phi[k] (+ 2 counts)
-//   lflag    int          per near-contact tile: already listed by the current phase pass
+//   lflag    2 x int      per near-contact tile and phi buffer: the tile is in that buffer's list
 //   red      reduction partials and result
 #include <algorithm>
 #include <climits>
@@ -43,16 +43,20 @@ cudaEvent_t take_event(lbm_ctx *c) {
   return e;
 }
 
-// Wraps one launch in a pair of events when the profiler is on.
-template <class F> cudaError_t timed(lbm_ctx *c, int kind, F &&launch, int kernels = 1) {
+// Wraps one launch (on stream s, default the context stream) in a pair of events when the
+// profiler is on.
+template <class F> cudaError_t timed_on(lbm_ctx *c, cudaStream_t s, int kind, F &&launch, int kernels = 1) {
   if (!c->prof || !((c->prof_mask >> kind) & 1u)) return launch();
   cudaEvent_t a = take_event(c), b = take_event(c);
   if (!a || !b) return cudaErrorMemoryAllocation;
-  cudaEventRecord(a, c->stream);
+  cudaEventRecord(a, s);
   cudaError_t e = launch();
-  cudaEventRecord(b, c->stream);
+  cudaEventRecord(b, s);
   c->pairs.push_back({kind, kernels, a, b});
   return e;
+}
+template <class F> cudaError_t timed(lbm_ctx *c, int kind, F &&launch, int kernels = 1) {
+  return timed_on(c, c->stream, kind, launch, kernels);
 }
 
 int validate(const lbm_params *p) {
@@ -162,9 +166,9 @@ int sync(lbm_ctx *c) { return from_cuda(cudaStreamSynchronize(c->stream)); }
 int finish_init(lbm_ctx *c) {
   int rc = from_cuda(cudaMemsetAsync(c->ntiles, 0, 2 * sizeof(int), c->stream));
   if (rc) return rc;
-  rc = from_cuda(cudaMemsetAsync(c->lflag, 0, sizeof(int) * tile_count(c->P.dim, c->K), c->stream));
+  rc = from_cuda(cudaMemsetAsync(c->lflag, 0, sizeof(int) * 2 * (size_t)c->ntile, c->stream));
   if (rc) return rc;
-  rc = from_cuda(launch_gate_tiles(c->P.dim, c->K, c->phi[c->pcur], c->tiles[c->pcur], c->ntiles + c->pcur, c->stream));
+  rc = from_cuda(launch_gate_tiles(c->P.dim, c->K, c->phi[c->pcur], tile_list(c, c->pcur), c->stream));
   if (rc) return rc;
   rc = from_cuda(launch_reduce(c->K, c->phi[c->pcur], c->u, c->red_part, c->red_out, c->stream));
   if (rc) return rc;
@@ -187,17 +191,72 @@ int run_moments(lbm_ctx *c) {
   if (c->P.nci_on) {
     rc = from_cuda(timed(c, LBM_K_NCI, [&] {
       return launch_nci(d, c->K, c->T, c->phi[c->pcur], c->nrm, c->frep, nullptr, 0, c->tiles[c->pcur],
-                        c->ntiles + c->pcur, c->nci_blocks, c->stream, nci_aux(c), c->lflag);
+                        c->ntiles + c->pcur, c->nci_blocks, c->stream, nci_aux(c), c->ntiles + (c->pcur ^ 1));
     }, nci_list_kernels(c)));
     if (rc) return rc;
   }
   return from_cuda(timed(c, LBM_K_HYDRO, [&] {
     return launch_hydro(c->P.Q, c->P.store, kMoments, c->K, c->pop[c->cur], nullptr, c->phi[c->pcur], c->frep,
-                        c->mom, c->mom + 3 * c->N, nullptr, c->stream);
+                        c->mom, c->mom + 3 * c->N, c->stream);
   }));
 }
 
 }  // namespace
+
+// One step's launches on stream s, from population buffer cur and phi buffer pcur, for a context
+// whose state is set: the near-contact pass over the tiles listed for phi^n (it also empties the
+// list of the other phi buffer, consumed by the previous step), the hydrodynamic pass, then the
+// phase-field pass. With lists, the phase-field pass lists the tiles of phi^{n+1} and clears the
+// marks of phi^n's list; without, the lists are left as they are (a dry step writes only the
+// next-step buffers and per-step scratch). Makes no non-stream CUDA call (it may be captured).
+int enqueue_step(lbm_ctx *c, int cur, int pcur, bool lists, cudaStream_t st) {
+  const int d = c->P.dim, nxt = cur ^ 1, pn = pcur ^ 1;
+  const bool nci = c->P.nci_on != 0;
+  int rc;
+  if (nci && c->overlap_blocks > 0 && c->side) {
+    // split step: the near-contact pass, then the listed tiles' hydrodynamics, on the side stream,
+    // while st updates every other tile (none of their cells is gated, so none reads frep)
+    const TileList listed = tile_list(c, pcur);
+    rc = from_cuda(cudaEventRecord(c->ev_fork, st));
+    if (!rc) rc = from_cuda(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    if (rc) return rc;
+    rc = from_cuda(timed_on(c, c->side, LBM_K_NCI, [&] {
+      return launch_nci(d, c->K, c->T, c->phi[pcur], c->nrm, c->frep, nullptr, 0, c->tiles[pcur], c->ntiles + pcur,
+                        c->overlap_blocks, c->side, nci_aux(c), c->ntiles + pn);
+    }, nci_list_kernels(c)));
+    if (rc) return rc;
+    rc = from_cuda(launch_hydro_split(1, c->P.Q, c->P.store, c->K, c->pop[cur], c->pop[nxt], c->phi[pcur], c->frep,
+                                      c->u, listed, c->split_blocks, c->side));
+    if (!rc) rc = from_cuda(cudaEventRecord(c->ev_join, c->side));
+    if (rc) return rc;
+    // the hydrodynamic pass as timed: from its first launch to the join of both parts
+    rc = from_cuda(timed_on(c, st, LBM_K_HYDRO, [&] {
+      cudaError_t e = launch_hydro_split(0, c->P.Q, c->P.store, c->K, c->pop[cur], c->pop[nxt], c->phi[pcur],
+                                         c->frep, c->u, listed, 0, st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->ev_join, 0);
+      return e;
+    }, 2));
+    if (rc) return rc;
+  } else {
+    if (nci) {
+      rc = from_cuda(timed_on(c, st, LBM_K_NCI, [&] {
+        return launch_nci(d, c->K, c->T, c->phi[pcur], c->nrm, c->frep, nullptr, 0, c->tiles[pcur],
+                          c->ntiles + pcur, c->nci_blocks, st, nci_aux(c), c->ntiles + pn);
+      }, nci_list_kernels(c)));
+      if (rc) return rc;
+    }
+    rc = from_cuda(timed_on(c, st, LBM_K_HYDRO, [&] {
+      return launch_hydro(c->P.Q, c->P.store, kStep, c->K, c->pop[cur], c->pop[nxt], c->phi[pcur], c->frep, c->u,
+                          nullptr, st);
+    }));
+    if (rc) return rc;
+  }
+  const bool upd = nci && lists;
+  return from_cuda(timed_on(c, st, LBM_K_PHASE, [&] {
+    return launch_phase(d, c->K, c->phi[pcur], c->u, c->phi[pn], upd ? tile_list(c, pn) : TileList{},
+                        upd ? tile_list(c, pcur) : TileList{}, st);
+  }));
+}
 
 extern "C" {
 
@@ -232,12 +291,13 @@ int lbm_create(const lbm_params *p, lbm_ctx **out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->frep, sizeof(float4) * c->N);
   if (e == cudaSuccess) e = cudaMalloc(&c->nrm, sizeof(float4) * c->N);
   const int ntile = tile_count(p->dim, c->K);
+  c->ntile = ntile;
   if (e == cudaSuccess) e = cudaMalloc(&c->tiles[0], sizeof(int) * ntile);
   if (e == cudaSuccess) e = cudaMalloc(&c->tiles[1], sizeof(int) * ntile);
   if (e == cudaSuccess) e = cudaMalloc(&c->ntiles, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->ntiles, 0, 2 * sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&c->lflag, sizeof(int) * ntile);
-  if (e == cudaSuccess) e = cudaMemset(c->lflag, 0, sizeof(int) * ntile);
+  if (e == cudaSuccess) e = cudaMalloc(&c->lflag, sizeof(int) * 2 * (size_t)ntile);
+  if (e == cudaSuccess) e = cudaMemset(c->lflag, 0, sizeof(int) * 2 * (size_t)ntile);
   if (e == cudaSuccess && p->nci_on && nci_aux_applies(p->dim, c->K)) {
     e = cudaMalloc(&c->aux.bricks, sizeof(uint4) * nci_brick_count(c->K));
     if (e == cudaSuccess) e = cudaMalloc(&c->aux.flags, (size_t)ntile);
@@ -249,6 +309,16 @@ int lbm_create(const lbm_params *p, lbm_ctx **out) {
   if (e == cudaSuccess) {
     c->nci_blocks = nci_list_blocks(p->dim);
     if (c->nci_blocks <= 0) e = cudaErrorInvalidConfiguration;
+  }
+  if (e == cudaSuccess && p->nci_on && hydro_split_applies(p->Q, c->K)) {
+    // the stream and events of the split step (lbm_set_overlap); it is off by default
+    int lo = 0, hi = 0;
+    e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    c->overlap_blocks = 0;
+    c->split_blocks = c->nci_blocks;
   }
   if (e == cudaSuccess) e = phase_prepare(p->dim);
   // the static scratch of lbm_mass_noalloc is taken here, once per device, while allocating is
@@ -271,6 +341,12 @@ int lbm_create(const lbm_params *p, lbm_ctx **out) {
 void lbm_destroy(lbm_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);  // the stream must outlive the context
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    cudaStreamDestroy(c->side);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   for (auto &pp : c->pairs) {
     cudaEventDestroy(pp.a);
     cudaEventDestroy(pp.b);
@@ -352,32 +428,25 @@ int lbm_get_state(lbm_ctx *c, double *f, double *phi) {
   return sync(c);
 }
 
+int lbm_set_overlap(lbm_ctx *c, int blocks) {
+  if (!c || blocks < 0) return LBM_ERR_ARG;
+  if (!c->side) return blocks == 0 ? LBM_OK : LBM_ERR_STATE;
+  c->overlap_blocks = std::min(blocks, c->nci_blocks);
+  return LBM_OK;
+}
+
+int lbm_get_overlap(const lbm_ctx *c, int *blocks) {
+  if (!c || !blocks) return LBM_ERR_ARG;
+  *blocks = c->side ? c->overlap_blocks : 0;
+  return LBM_OK;
+}
+
 int lbm_step(lbm_ctx *c, int n) {
   if (!c || n < 0) return LBM_ERR_ARG;
   if (!c->initialised) return LBM_ERR_STATE;
-  const int d = c->P.dim;
   for (int s = 0; s < n; s++) {
     const int nxt = c->cur ^ 1, pn = c->pcur ^ 1;
-    int rc;
-    // near-contact pass over the tiles listed for phi^n; the hydrodynamic pass then clears that
-    // list's count, and the phase-field pass lists the tiles of phi^{n+1}
-    const bool nci = c->P.nci_on != 0;
-    if (nci) {
-      rc = from_cuda(timed(c, LBM_K_NCI, [&] {
-        return launch_nci(d, c->K, c->T, c->phi[c->pcur], c->nrm, c->frep, nullptr, 0, c->tiles[c->pcur],
-                          c->ntiles + c->pcur, c->nci_blocks, c->stream, nci_aux(c), c->lflag);
-      }, nci_list_kernels(c)));
-      if (rc) return rc;
-    }
-    rc = from_cuda(timed(c, LBM_K_HYDRO, [&] {
-      return launch_hydro(c->P.Q, c->P.store, kStep, c->K, c->pop[c->cur], c->pop[nxt], c->phi[c->pcur], c->frep,
-                          c->u, nullptr, nci ? c->ntiles + c->pcur : nullptr, c->stream);
-    }));
-    if (rc) return rc;
-    rc = from_cuda(timed(c, LBM_K_PHASE, [&] {
-      return launch_phase(d, c->K, c->phi[c->pcur], c->u, c->phi[pn], nci ? c->tiles[pn] : nullptr,
-                          nci ? c->ntiles + pn : nullptr, c->lflag, c->stream);
-    }));
+    int rc = enqueue_step(c, c->cur, c->pcur, true, c->stream);
     if (rc) return rc;
     c->cur = nxt;
     c->pcur = pn;
@@ -488,7 +557,7 @@ int lbm_nci_diagnostics(lbm_ctx *c, double *out) {
   // the near-contact pass over the tiles listed for the current phi (the list stays for the next step)
   int rc = from_cuda(timed(c, LBM_K_NCI, [&] {
     return launch_nci(c->P.dim, c->K, c->T, c->phi[c->pcur], c->nrm, c->frep, nullptr, 0, c->tiles[c->pcur],
-                      c->ntiles + c->pcur, c->nci_blocks, c->stream, nci_aux(c), c->lflag);
+                      c->ntiles + c->pcur, c->nci_blocks, c->stream, nci_aux(c), c->ntiles + (c->pcur ^ 1));
   }, nci_list_kernels(c)));
   if (rc) return rc;
   rc = from_cuda(timed(c, LBM_K_REDUCE, [&] {

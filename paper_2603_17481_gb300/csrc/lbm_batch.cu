@@ -69,7 +69,7 @@ bool fusable(lbm_ctx *const *ctxs, int n) {
 // The near-contact pass of context c on phi[pc] (the list of that buffer), on stream s.
 cudaError_t nci_pass(lbm_ctx *c, int pc, cudaStream_t s) {
   return launch_nci(c->P.dim, c->K, c->T, c->phi[pc], c->nrm, c->frep, nullptr, 0, c->tiles[pc], c->ntiles + pc,
-                    c->nci_blocks, s, nci_aux(c), c->lflag);
+                    c->nci_blocks, s, nci_aux(c), c->ntiles + (pc ^ 1));
 }
 
 // BatchCase of context c for a step from buffer parity (cur, pcur); lists = false leaves the
@@ -84,10 +84,10 @@ BatchCase batch_case(lbm_ctx *c, int cur, int pcur, bool lists) {
   b.frep = c->frep;
   b.u = c->u;
   const bool nci = lists && c->P.nci_on;
-  b.reset = nci ? c->ntiles + pcur : nullptr;
-  b.tiles = nci ? c->tiles[pcur ^ 1] : nullptr;
-  b.ntiles = nci ? c->ntiles + (pcur ^ 1) : nullptr;
-  b.lflag = c->lflag;
+  if (nci) {
+    b.next = tile_list(c, pcur ^ 1);
+    b.prev = tile_list(c, pcur);
+  }
   b.ncx = (c->P.nx + March3::OUT - 1) / March3::OUT;
   return b;
 }
@@ -183,12 +183,11 @@ int time_dry_step(lbm_batch *b, bool fused, double &ms) {
     lbm_ctx *c = b->ctxs[i];
     const cudaStream_t br = b->branches[i % b->branches.size()];
     const int cur = b->cur0[i], pc = b->pcur0[i];
-    if (c->P.nci_on) e = nci_pass(c, pc, br);
-    if (!fused && e == cudaSuccess)
-      e = launch_hydro(c->P.Q, c->P.store, kStep, c->K, c->pop[cur], c->pop[cur ^ 1], c->phi[pc], c->frep, c->u,
-                       nullptr, nullptr, br);
-    if (!fused && e == cudaSuccess)
-      e = launch_phase(c->P.dim, c->K, c->phi[pc], c->u, c->phi[pc ^ 1], nullptr, nullptr, c->lflag, br);
+    if (fused) {
+      if (c->P.nci_on) e = nci_pass(c, pc, br);
+    } else if (enqueue_step(c, cur, pc, false, br) != LBM_OK) {
+      e = cudaErrorUnknown;
+    }
   }
   for (size_t s = 0; s < b->branches.size() && e == cudaSuccess; s++) {
     e = cudaEventRecord(b->joins[s], b->branches[s]);
@@ -269,16 +268,7 @@ int capture_steps(lbm_batch *b, int g) {
       if (b->fused) {
         if (c->P.nci_on) e = nci_pass(c, b->pcur0[i] ^ q, br);
       } else {
-        const cudaStream_t saved = c->stream;
-        const long long steps = c->steps;
-        c->stream = br;
-        c->cur = b->cur0[i] ^ q;
-        c->pcur = b->pcur0[i] ^ q;
-        rc = lbm_step(c, 1);
-        c->stream = saved;
-        c->cur = b->cur0[i];  // capture runs nothing: the contexts keep their state
-        c->pcur = b->pcur0[i];
-        c->steps = steps;
+        rc = enqueue_step(c, b->cur0[i] ^ q, b->pcur0[i] ^ q, true, br);
       }
     }
     for (size_t s = 0; s < b->branches.size() && e == cudaSuccess; s++) {

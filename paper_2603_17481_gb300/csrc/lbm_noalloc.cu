@@ -70,10 +70,10 @@ extern "C" int lbm_mass_noalloc(lbm_ctx *c, double *phi_mass, double *mom) {
   cudaError_t e = cudaSuccess;
   if (c->P.nci_on)
     e = launch_nci(c->P.dim, c->K, c->T, c->phi[c->pcur], c->nrm, c->frep, nullptr, 0, c->tiles[c->pcur],
-                   c->ntiles + c->pcur, c->nci_blocks, c->stream, nci_aux(c), c->lflag);
+                   c->ntiles + c->pcur, c->nci_blocks, c->stream, nci_aux(c), c->ntiles + (c->pcur ^ 1));
   if (e == cudaSuccess)
     e = launch_hydro(c->P.Q, c->P.store, kMoments, c->K, c->pop[c->cur], nullptr, c->phi[c->pcur], c->frep,
-                     c->mom, c->mom + 3 * c->N, nullptr, c->stream);
+                     c->mom, c->mom + 3 * c->N, c->stream);
   if (e == cudaSuccess)
     e = launch_reduce_n(c->K, c->phi[c->pcur], c->mom, scratch, (int)nblocks, scratch + kMaxBlocks, c->stream);
   ReduceOut r;

@@ -263,13 +263,22 @@ __device__ __forceinline__ void march_run(const KParams &P, const int32_t *__res
   }
 }
 
+// Clears the marks of the near-contact list of phi, whose step is done (every thread of the grid
+// takes a share of the list).
+__device__ __forceinline__ void clear_marks(const TileList &prev, const long long rank, const long long threads) {
+  if (!prev.mark) return;
+  const int n = *prev.count;
+  for (long long i = rank; i < n; i += threads) prev.mark[prev.tiles[i]] = 0;
+}
+
 // The grid's warps share the (column, plane) units of one case equally.
 template <int M>
 __global__ void __launch_bounds__(March3::NT, LBM_MARCH_MINB)
 k_phase3m(const KParams P, const int32_t *__restrict__ phi, const float *__restrict__ u,
-          int32_t *__restrict__ phi_out, int *__restrict__ tiles, int *__restrict__ ntiles, int *__restrict__ lflag,
-          const int ncx, const long long units) {
+          int32_t *__restrict__ phi_out, const TileList next, const TileList prev, const int ncx,
+          const long long units) {
   pdl_enter();
+  clear_marks(prev, (long long)blockIdx.x * March3::NT + threadIdx.x, (long long)gridDim.x * March3::NT);
   const long long nwarps = (long long)gridDim.x * March3::WARPS;
   const long long wid = (long long)blockIdx.x * March3::WARPS + (threadIdx.x >> 5);
   long long ub = units * wid / nwarps;
@@ -280,7 +289,7 @@ k_phase3m(const KParams P, const int32_t *__restrict__ phi, const float *__restr
     const int z0 = (int)(ub - col * nz);
     const int z1 = (int)min((long long)nz, (long long)z0 + (ue - ub));
     ub += z1 - z0;
-    march_run<M>(P, phi, u, phi_out, tiles, ntiles, lflag, ncx, col, z0, z1);
+    march_run<M>(P, phi, u, phi_out, next.tiles, next.count, next.mark, ncx, col, z0, z1);
   }
 }
 

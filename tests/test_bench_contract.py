@@ -52,6 +52,7 @@ def test_repo_arm_plan_has_no_negative_step_count(argv):
     assert plan["variant_stores"] == ("f16", "bf16")
     assert plan["early"] == bm.EARLY and plan["late"] == bm.LATE and bm.EARLY < bm.LATE
     assert plan["variant_timed"] >= 1 and plan["split_steps"] >= 1 and plan["e2e_steps"] >= 1
+    assert plan["split_compare_steps"] >= 1
     assert plan["cpu_baseline"] is True
     # other ranks and multi-GPU runs skip the variants and the CPU baseline
     p2 = bm.run_plan(args, world=2, rank=1)

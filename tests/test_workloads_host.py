@@ -91,9 +91,15 @@ def test_workload_extras_do_not_shadow_parameters():
 
 def test_kernels_per_step():
     """Kernel launches of one step as the bench claims them: the brick prefilter adds one kernel on 3D
-    grids whose sides are multiples of 4."""
+    grids whose sides are multiples of 4, and the split step (3D, near-contact on, nx even) runs the
+    hydrodynamic update as two launches."""
     assert bench.kernels_per_step(W.base_config(3, 64, 48, 40, 19)) == 5
-    assert bench.kernels_per_step(W.base_config(3, 37, 21, 13, 19)) == 4
+    assert bench.kernels_per_step(W.base_config(3, 64, 48, 40, 19), overlap=True) == 6
+    assert bench.kernels_per_step(W.base_config(3, 37, 21, 13, 19), overlap=True) == 4
+    assert bench.kernels_per_step(W.base_config(3, 38, 21, 13, 19), overlap=True) == 5
     assert bench.kernels_per_step(W.base_config(3, 64, 48, 40, 19, nci_on=0)) == 2
     assert bench.kernels_per_step(W.base_config(2, 128, 64, 1, 9)) == 4
     assert all(bench.kernels_per_step(c) == 5 for c in W.collision_sweep(8))
+    assert all(bench.nci_kernels(c) == 3 for c in W.collision_sweep(8))
+    big = W.base_config(3, 1024, 1024, 256, 27)  # Q N > 2^32: 64-bit offsets, one launch
+    assert not bench.split_applies(big) and bench.kernels_per_step(big, overlap=True) == 5
