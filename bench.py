@@ -68,6 +68,18 @@ def hydro_bytes_per_cell(Q, pop_bytes):
     return 2 * Q * pop_bytes + 4 + 12
 
 
+RECORD_BYTES = 64  # the moment-record store: one 16-float record per cell instead of Q populations
+
+
+def store_bytes_per_cell(Q, store):
+    """(hydro kernel, whole step) algorithmic bytes per cell update for a store: populations (or
+    records) read + written, phi read (+ written by phase), velocity written + read."""
+    if store == "mom":
+        return 2 * RECORD_BYTES + 4 + 12, 2 * RECORD_BYTES + 8 + 24
+    pb = 4 if store == "f32" else 2
+    return hydro_bytes_per_cell(Q, pb), step_bytes_per_cell(Q, pb)
+
+
 # DRAM traffic of one hydrodynamic launch on the full workload, from the ncu capture summarised in
 # profiles/ (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hydro kernel source hash:
 # a changed kernel reports null until it is profiled again.
@@ -237,7 +249,7 @@ def run_plan(args, world, rank):
         "split_steps": max(min(args.steps, 500), 1),
         "split_compare_steps": max(min(args.steps, 500), 1),
         "e2e_steps": max(args.steps, 1) if not args.no_e2e else 0,
-        "variant_stores": ("f16", "bf16") if variants else (),
+        "variant_stores": ("f16", "bf16", "mom") if variants else (),
         "variant_timed": max(args.steps, 1), "early": EARLY, "late": LATE,
         "cpu_baseline": rank == 0 and world == 1 and not args.no_cpu_baseline,
     }
@@ -312,18 +324,18 @@ def run_ours(args, world, rank, local):
             split_step[f"scan_blocks_{blocks}"] = {"value": round(mo, 1), "vs_one_stream": round(mo / (mlups / world), 4)}
         sim.set_overlap(0)
 
-    pop_b = 4 if args.store == "f32" else 2
+    hydro_b, step_b = store_bytes_per_cell(Q, args.store)
     peak, peak_kind = measured_peaks()
     # one hydrodynamic pass per step
     hydro_ms, _ = prof["hydro"]
     hydro_avg = hydro_ms / max(plan["timed"], 1)
-    per_launch_bytes = hydro_bytes_per_cell(Q, pop_b) * N
+    per_launch_bytes = hydro_b * N
     achieved = per_launch_bytes / (hydro_avg * 1e-3) / 1e9
     key = (args.store, Q, _src_hash("hydro_impl.cuh", "lbm_device.cuh"))
     traffic = HYDRO_TRAFFIC.get(key)
     gpu_launches = kernels_per_step(cfg) * args.steps
 
-    step_frac = mlups / world * 1e6 * step_bytes_per_cell(Q, pop_b) / (peak * 1e9)
+    step_frac = mlups / world * 1e6 * step_b / (peak * 1e9)
 
     # end-to-end through the C ABI with pinned host buffers: H2D of the initial fields, one
     # lbm_step call per step, D2H of the final fields
@@ -390,9 +402,9 @@ def run_ours(args, world, rank, local):
             ph_late = fresh(st, plan["late"])
             variants[st] = {
                 "value": round(v_mlups, 1), "steps": kv, "vs_f32": round(v_mlups / mlups, 4),
-                "hydro_gbs": round(hydro_bytes_per_cell(Q, 2) * N / (hm / kv * 1e-3) / 1e9, 1),
+                "hydro_gbs": round(store_bytes_per_cell(Q, st)[0] * N / (hm / kv * 1e-3) / 1e9, 1),
                 "hydro_ms": round(hm / kv, 5),
-                "step_roofline_frac": round(v_mlups * 1e6 * step_bytes_per_cell(Q, 2) / (peak * 1e9), 4),
+                "step_roofline_frac": round(v_mlups * 1e6 * store_bytes_per_cell(Q, st)[1] / (peak * 1e9), 4),
                 "phi_diff_vs_f32": {
                     f"after_{plan['early']}_steps": {"max": float(d_early.max()),
                                                      "q999": float(np.quantile(d_early, 0.999))},
@@ -410,7 +422,9 @@ def run_ours(args, world, rank, local):
                          f"{tt:.1f} s, OpenMP over all host cores"}
         # every store against the FP64 oracle after the same steps, on the full grid
         vs_oracle = {"steps": steps}
-        for st in ("f32",) + tuple(plan["variant_stores"]):
+        # (the record store starts from the equilibrium records, which stream f_eq of the
+        # neighbours: another initial state, compared with the oracle in the parity tests)
+        for st in ("f32",) + tuple(v for v in plan["variant_stores"] if v != "mom"):
             s = B.Lbm(cfg, store=st, stream=stream.cuda_stream)
             s.init_fields(phi, u)
             s.step(steps)
@@ -429,13 +443,14 @@ def run_ours(args, world, rank, local):
         "config": {"workload": WORKLOAD.format(Q=Q), "cells": N,
                    "lattice": f"D3Q{Q} hydro, D3Q27 phase-field stencils",
                    "store": args.store, "near_contact": "on (w=3, q_th=0.125, eta=0.1, cos=-0.8)",
-                   "l2": "inputs larger than L2 (2 x %.0f MB populations), no flush" % (Q * N * pop_b / 1e6),
+                   "l2": "inputs larger than L2 (2 x %.0f MB %s), no flush" % (
+                       (hydro_b - 16) / 2 * N / 1e6, "records" if args.store == "mom" else "populations"),
                    "parallelism": f"{world} independent replica(s), one per GPU"},
         "roofline": {"bound": "hbm", "kernel": "hydro", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "bytes_per_cell": hydro_bytes_per_cell(Q, pop_b), "avg_ms": round(hydro_avg, 5),
+                     "bytes_per_cell": hydro_b, "avg_ms": round(hydro_avg, 5),
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"},
-        "step_roofline": {"bytes_per_cell": step_bytes_per_cell(Q, pop_b), "frac_of_measured": round(step_frac, 4),
+        "step_roofline": {"bytes_per_cell": step_b, "frac_of_measured": round(step_frac, 4),
                           "frac_of_8TBs": round(step_frac * peak / 8000.0, 4)},
         "kernels_ms_per_step": {k: round(ms / split_steps, 5) for k, (ms, n) in split.items() if n},
         "kernels_split_steps": split_steps,
@@ -884,7 +899,7 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--store", choices=["f32", "f16", "bf16"], default="f32")
+    ap.add_argument("--store", choices=["f32", "f16", "bf16", "mom"], default="f32")
     ap.add_argument("--lattice", type=int, choices=[19, 27], default=19,
                     help="collision: hydrodynamic lattice D3Q19 (the benchmark's) or D3Q27 (the paper's)")
     ap.add_argument("--no-e2e", action="store_true")

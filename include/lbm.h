@@ -50,7 +50,14 @@ typedef enum {
 typedef enum {
   LBM_STORE_F32 = 0,  /* populations stored as FP32                                             */
   LBM_STORE_F16 = 1,  /* populations stored as FP16, f_i / w_i (deviation from rest, p* = 0)    */
-  LBM_STORE_BF16 = 2  /* populations stored as BF16, f_i / w_i                                  */
+  LBM_STORE_BF16 = 2, /* populations stored as BF16, f_i / w_i                                  */
+  LBM_STORE_MOMENTS = 3 /* 3D only: per cell the FP32 record of its post-collision state (the     */
+                      /* thread-safe moment representation of Sec. 2.1): p*, u, F / rho and the  */
+                      /* relaxed regularized A2 of Eq. 14, as 16 floats (64 B instead of 4 Q B); */
+                      /* a cell pulls f_i by evaluating Eqs. 11, 15-17 and the Guo term at the    */
+                      /* record of x - c_i. lbm_init_fields stores the record of f_eq(p*, u) at   */
+                      /* every cell, so the first step pulls f_eq_i of x - c_i; lbm_set_state is  */
+                      /* refused (LBM_ERR_STATE): arbitrary populations have no record form.      */
 } lbm_store;
 
 /* Kernel kinds reported by the profiler (lbm_profile_read). */

@@ -16,8 +16,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "liblbm.so")
 
 LBM_OK, LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_UNSTABLE, LBM_ERR_STATE = 0, -1, -2, -3, -4, -5
-LBM_STORE_F32, LBM_STORE_F16, LBM_STORE_BF16 = 0, 1, 2
-STORES = {"f32": LBM_STORE_F32, "f16": LBM_STORE_F16, "bf16": LBM_STORE_BF16}
+LBM_STORE_F32, LBM_STORE_F16, LBM_STORE_BF16, LBM_STORE_MOMENTS = 0, 1, 2, 3
+STORES = {"f32": LBM_STORE_F32, "f16": LBM_STORE_F16, "bf16": LBM_STORE_BF16, "mom": LBM_STORE_MOMENTS}
 KERNEL_KINDS = ("nci", "hydro", "phase", "reduce", "convert")
 NO_PARTNER = np.iinfo(np.int32).min
 

@@ -38,10 +38,14 @@
 
 namespace lbm {
 
+// hydro_cell's third mode: the post-collision state as a moment record (sink(q0, q1, q2, q3)).
+constexpr int kEmitRecord = 2;
+
 // The per-cell physics of a step after the pull and the phi stencils: mixture properties, the
 // force split, the velocity, then (MODE kStep) the regularized collision, handing each
-// post-collision population f_i / w_i to sink(i, value). ph, g and lap are phi, its isotropic
-// gradient and Laplacian at the cell; fr the near-contact force (zero where none was written).
+// post-collision population f_i / w_i to sink(i, value), or (kEmitRecord) its moment record.
+// ph, g and lap are phi, its isotropic gradient and Laplacian at the cell; fr the near-contact
+// force (zero where none was written).
 template <class L, int MODE, class Sink>
 __device__ __forceinline__ void hydro_cell(const KParams &P, const float (&f)[L::Q], const float ph, const float g0,
                                            const float g1, const float g2, const float lap, const float4 fr,
@@ -119,6 +123,12 @@ __device__ __forceinline__ void hydro_cell(const KParams &P, const float (&f)[L:
   const float om1 = 1.0f - omega;
   const float C0 = ps - 1.5f * uu - 1.5f * om1 * trA - 1.5f * ur;
   const float C1 = 3.0f - 4.5f * uu - 4.5f * om1 * trA;
+  if constexpr (MODE == kEmitRecord) {
+    // moment-record storage: the post-collision state itself (its populations are evaluated by
+    // the cells that pull them)
+    sink(make_float4(C0, C1, u0, u1), make_float4(u2, r0, r1, r2),
+         make_float4(om1 * A00, om1 * A11, om1 * A22, om1 * A01), make_float4(om1 * A02, om1 * A12, 0.f, 0.f));
+  } else {
   const float k45 = 4.5f * om1, k135 = 13.5f * om1, k9 = 9.0f * om1;
 
   sink(0, C0);
@@ -187,6 +197,7 @@ __device__ __forceinline__ void hydro_cell(const KParams &P, const float (&f)[L:
       sink(ia, ev + od);
       sink(L::opp(ia), ev - od);
     }
+  }
   }
 }
 
@@ -339,7 +350,8 @@ __device__ __forceinline__ void hydro_cell_pair(const KParams &P, const V2 (&f)[
 // checked by the launcher), so a pull or store address is one 32-bit multiply-add and one widening
 // add; otherwise the offsets are 64-bit.
 template <class L, int S, int MODE, bool I32>
-__global__ void __launch_bounds__(Tile<L::D>::X * Tile<L::D>::Y * Tile<L::D>::Z, L::Q >= 27 ? 4 : LBM_HYDRO_MINB)
+__global__ void __launch_bounds__(Tile<L::D>::X * Tile<L::D>::Y * Tile<L::D>::Z,
+                                  S == kStoreRecord ? 3 : (L::Q >= 27 ? 4 : LBM_HYDRO_MINB))
 k_hydro(const KParams P, const typename Store<S>::T *__restrict__ src, typename Store<S>::T *__restrict__ dst,
         const int32_t *__restrict__ phi, const float4 *__restrict__ frep, float *__restrict__ u_out,
         float *__restrict__ ps_out) {
@@ -391,12 +403,17 @@ k_hydro(const KParams P, const typename Store<S>::T *__restrict__ src, typename 
   using Off = typename std::conditional<I32, unsigned, long long>::type;
   const Off NO = (Off)N;
 
-  // pull: f_i(x) = src_i(x - c_i)
+  // pull: f_i(x) = src_i(x - c_i), or evaluated from the moment record of x - c_i
   float f[L::Q];
 #pragma unroll
   for (int i = 0; i < L::Q; i++) {
     const int s = X[1 - L::c(i, 0)] + RB[1 - L::c(i, 1)][1 - L::c(i, 2)];
-    f[i] = Store<S>::ld(src + ((Off)i * NO + (Off)s), L::w(i));
+    if constexpr (S == kStoreRecord) {
+      const float4 *q = src + (Off)s;
+      f[i] = L::w(i) * record_f_over_w<L>(i, __ldg(q), __ldg(q + NO), __ldg(q + 2 * NO), __ldg(q + 3 * NO));
+    } else {
+      f[i] = Store<S>::ld(src + ((Off)i * NO + (Off)s), L::w(i));
+    }
   }
 
   // isotropic gradient and Laplacian of phi (Eqs. 22-23)
@@ -422,8 +439,16 @@ k_hydro(const KParams P, const typename Store<S>::T *__restrict__ src, typename 
   float4 fr = make_float4(0.f, 0.f, 0.f, 0.f);
   if (P.nci_on && q_gate_value(v) >= P.q_th) fr = __ldg(frep + idx);
   float u0, u1, u2, ps;
-  hydro_cell<L, MODE>(P, f, ph, g0, g1, g2, lap, fr, u0, u1, u2, ps,
-                      [&](int i, float vw) { Store<S>::st_w(dst + ((Off)i * NO + (Off)idx), vw, L::w(i)); });
+  if constexpr (S == kStoreRecord && MODE == kStep) {
+    float4 *q = dst + (Off)idx;
+    hydro_cell<L, kEmitRecord>(P, f, ph, g0, g1, g2, lap, fr, u0, u1, u2, ps, [&](float4 a, float4 b, float4 c, float4 d) {
+      q[0] = a; q[NO] = b; q[2 * NO] = c; q[3 * NO] = d;
+    });
+  } else {
+    hydro_cell<L, MODE>(P, f, ph, g0, g1, g2, lap, fr, u0, u1, u2, ps, [&](int i, float vw) {
+      if constexpr (S != kStoreRecord) Store<S>::st_w(dst + ((Off)i * NO + (Off)idx), vw, L::w(i));
+    });  // (with the record store only kMoments reaches here, which stores no population)
+  }
   if (MODE == kMoments) {
     u_out[idx] = u0;
     u_out[NO + (Off)idx] = u1;
@@ -692,7 +717,7 @@ cudaError_t launch_hydro_t(int mode, const KParams &P, const void *src, void *ds
   const T *a = (const T *)src;
   T *b = (T *)dst;
   const int *all = nullptr;
-  if constexpr (L::D == 3) {
+  if constexpr (L::D == 3 && S != kStoreRecord) {
     if (i32 && P.nx % 2 == 0) {
       dim3 g2((P.nx + 63) / 64, (P.ny + 3) / 4, (P.nz + 1) / 2);
       return mode == kStep ? launch_pdl(k_hydro2<L, S, kStep>, g2, block, 0, s, P, a, b, phi, frep, u, pstar, all)
@@ -712,7 +737,11 @@ cudaError_t launch_hydro_lattice(int store, int mode, const KParams &P, const vo
   switch (store) {
     case 0: return launch_hydro_t<L, 0>(mode, P, src, dst, phi, frep, u, pstar, s);
     case 1: return launch_hydro_t<L, 1>(mode, P, src, dst, phi, frep, u, pstar, s);
-    default: return launch_hydro_t<L, 2>(mode, P, src, dst, phi, frep, u, pstar, s);
+    case 2: return launch_hydro_t<L, 2>(mode, P, src, dst, phi, frep, u, pstar, s);
+    case kStoreRecord:
+      if constexpr (L::D == 3) return launch_hydro_t<L, kStoreRecord>(mode, P, src, dst, phi, frep, u, pstar, s);
+      return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
   }
 }
 
@@ -738,7 +767,8 @@ cudaError_t launch_split_lattice(int part, int store, const KParams &P, const vo
   switch (store) {
     case 0: return launch_split_t<L, 0>(part, P, src, dst, phi, frep, u, listed, blocks, s);
     case 1: return launch_split_t<L, 1>(part, P, src, dst, phi, frep, u, listed, blocks, s);
-    default: return launch_split_t<L, 2>(part, P, src, dst, phi, frep, u, listed, blocks, s);
+    case 2: return launch_split_t<L, 2>(part, P, src, dst, phi, frep, u, listed, blocks, s);
+    default: return cudaErrorInvalidValue;  // the paired kernel stores populations
   }
 }
 

@@ -135,10 +135,44 @@ __global__ void k_get_pops(const KParams P, const typename Store<S>::T *__restri
   }
 }
 
+// Moment-record storage: the record of the equilibrium f_eq(p*, u) at every cell (B = 0, r = 0),
+// so that cell x pulls f_eq_i of x - c_i at the first step.
+__global__ void k_init_record(const KParams P, const double *__restrict__ u64, const double *__restrict__ ps64,
+                              float4 *__restrict__ rec) {
+  long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= P.N) return;
+  const double u0 = u64[n], u1 = u64[P.N + n], u2 = u64[2 * P.N + n];
+  const double ps = ps64 ? ps64[n] : 0.0;
+  const double uu = u0 * u0 + u1 * u1 + u2 * u2;
+  rec[n] = make_float4((float)(ps - 1.5 * uu), (float)(3.0 - 4.5 * uu), (float)u0, (float)u1);
+  rec[P.N + n] = make_float4((float)u2, 0.f, 0.f, 0.f);
+  rec[2 * P.N + n] = make_float4(0.f, 0.f, 0.f, 0.f);
+  rec[3 * P.N + n] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Pre-collision populations f[i][x] of the moment-record state: direction i of the record of x - c_i.
+template <class L>
+__global__ void k_get_record(const KParams P, const float4 *__restrict__ rec, double *__restrict__ f64) {
+  long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= P.N) return;
+  int x = (int)(n % P.nx), y = (int)((n / P.nx) % P.ny), z = (int)(n / ((long long)P.nx * P.ny));
+#pragma unroll
+  for (int i = 0; i < L::Q; i++) {
+    const float4 *q = rec + cell_shift(P, x, y, z, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2), L::D);
+    f64[(long long)i * P.N + n] = (double)(L::w(i) * record_f_over_w<L>(i, q[0], q[P.N], q[2 * P.N], q[3 * P.N]));
+  }
+}
+
 template <class L>
 static cudaError_t pops_dispatch_l(int what, int store, const KParams &P, const double *a, const double *b,
                                    void *pops, double *out, cudaStream_t s) {
   dim3 g = grid1d(P.N, 128);
+  if (store == kStoreRecord) {  // 3D only; populations cannot be set in record form
+    if (L::D != 3 || what == 1) return cudaErrorInvalidValue;
+    if (what == 0) k_init_record<<<g, 128, 0, s>>>(P, a, b, (float4 *)pops);
+    else k_get_record<L><<<g, 128, 0, s>>>(P, (const float4 *)pops, out);
+    return cudaGetLastError();
+  }
 #define LBM_POPS_CASE(SV)                                                                              \
   case SV: {                                                                                           \
     using T = typename Store<SV>::T;                                                                   \

@@ -65,7 +65,8 @@ int validate(const lbm_params *p) {
   if (p->nx < 1 || p->ny < 1 || p->nz < 1) return LBM_ERR_ARG;
   if (p->dim == 2 && (p->nz != 1 || p->Q != 9)) return LBM_ERR_ARG;
   if (p->dim == 3 && p->Q != 19 && p->Q != 27) return LBM_ERR_ARG;
-  if (p->store < LBM_STORE_F32 || p->store > LBM_STORE_BF16) return LBM_ERR_ARG;
+  if (p->store < LBM_STORE_F32 || p->store > LBM_STORE_MOMENTS) return LBM_ERR_ARG;
+  if (p->store == LBM_STORE_MOMENTS && p->dim != 3) return LBM_ERR_ARG;
   long long N = (long long)p->nx * p->ny * p->nz;
   if (N > (long long)INT_MAX) return LBM_ERR_ARG;
   if (!(p->rho_l > 0) || !(p->rho_g > 0) || !(p->nu_l > 0) || !(p->nu_g > 0)) return LBM_ERR_ARG;
@@ -124,7 +125,11 @@ void build_table(int dim, int w, NciTable &T) {
     T.o[i] = NciOffset{(int8_t)v[i].dx, (int8_t)v[i].dy, (int8_t)v[i].dz, (int8_t)v[i].d2};
 }
 
-size_t store_size(int store) { return store == LBM_STORE_F32 ? 4 : 2; }
+// bytes of one population buffer
+size_t store_bytes(const lbm_params &p, long long N) {
+  if (p.store == LBM_STORE_MOMENTS) return sizeof(float4) * kRecordWords * (size_t)N;
+  return (size_t)p.Q * (size_t)N * (p.store == LBM_STORE_F32 ? 4 : 2);
+}
 
 int ensure_stage(lbm_ctx *c, size_t bytes) {
   if (c->stage_bytes >= bytes) return LBM_OK;
@@ -281,7 +286,7 @@ int lbm_create(const lbm_params *p, lbm_ctx **out) {
   derive_kparams(*p, c->K);
   build_table(p->dim, p->nci_on ? p->w : 1, c->T);
   c->N = c->K.N;
-  c->pop_bytes = (size_t)p->Q * (size_t)c->N * store_size(p->store);
+  c->pop_bytes = store_bytes(*p, c->N);
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaMalloc(&c->pop[0], c->pop_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&c->pop[1], c->pop_bytes);
@@ -310,7 +315,7 @@ int lbm_create(const lbm_params *p, lbm_ctx **out) {
     c->nci_blocks = nci_list_blocks(p->dim);
     if (c->nci_blocks <= 0) e = cudaErrorInvalidConfiguration;
   }
-  if (e == cudaSuccess && p->nci_on && hydro_split_applies(p->Q, c->K)) {
+  if (e == cudaSuccess && p->nci_on && p->store != LBM_STORE_MOMENTS && hydro_split_applies(p->Q, c->K)) {
     // the stream and events of the split step (lbm_set_overlap); it is off by default
     int lo = 0, hi = 0;
     e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
@@ -391,6 +396,7 @@ int lbm_init_fields(lbm_ctx *c, const double *phi, const double *u, const double
 
 int lbm_set_state(lbm_ctx *c, const double *f, const double *phi) {
   if (!c || !f || !phi) return LBM_ERR_ARG;
+  if (c->P.store == LBM_STORE_MOMENTS) return LBM_ERR_STATE;  // arbitrary f has no record form
   const long long N = c->N;
   const int Q = c->P.Q;
   int rc = ensure_stage(c, sizeof(double) * (size_t)(Q + 1) * N);

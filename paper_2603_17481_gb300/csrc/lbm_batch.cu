@@ -61,6 +61,7 @@ bool fusable(lbm_ctx *const *ctxs, int n) {
   for (int i = 0; i < n; i++) {
     const lbm_params &p = ctxs[i]->P;
     if (p.dim != 3 || p.Q != p0.Q || p.store != p0.store || p.nx % 2 != 0) return false;
+    if (p.store == LBM_STORE_MOMENTS) return false;  // the batched kernel stores populations
     if ((long long)p.Q * ctxs[i]->N > (1LL << 32)) return false;
   }
   return true;

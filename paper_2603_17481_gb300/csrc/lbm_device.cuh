@@ -106,6 +106,45 @@ template <> struct Store<2> {
   __device__ static __forceinline__ void st_w(T *p, float v_over_w, float) { *p = __float2bfloat16_rn(v_over_w); }
 };
 
+// Moment-record storage (the paper's thread-safe representation, Sec. 2.1): instead of Q
+// populations a cell stores the 16-float record of its post-collision state, four float4 kept as
+// four arrays of N float4 (buf[k * N + n] = q_k of cell n, so a warp's loads of one q_k are 512
+// contiguous bytes):
+//   q0 = (C0, C1, u0, u1), q1 = (u2, r0, r1, r2), q2 = (B00, B11, B22, B01), q3 = (B02, B12, 0, 0)
+// with r = F / rho, B = (1 - omega) A2 (the regularized non-equilibrium moment of Eq. 14 after
+// relaxation), C0 = p* - 1.5 |u|^2 - 1.5 tr B - 1.5 u.r and C1 = 3 - 4.5 |u|^2 - 4.5 tr B. The
+// post-collision population of direction c is then (Eqs. 3, 11, 15-17 with cs^2 = 1/3)
+//   f / w = E + O,  E = C0 + 4.5 (c.u)(c.u + c.r) + 4.5 c.B.c,
+//                   O = (c.u)(C1 + 4.5 (c.u)^2 + 13.5 c.B.c) - 9 c.B.u + 1.5 c.r,
+// so a cell pulls f_i(x) by evaluating this at the record of x - c_i.
+constexpr int kStoreRecord = 3;
+template <> struct Store<kStoreRecord> {
+  using T = float4;
+};
+constexpr int kRecordWords = 4;  // float4 per cell (arrays of the buffer)
+
+// f_i / w_i of direction i of the record (q0, q1, q2, q3)
+template <class L>
+__device__ __forceinline__ float record_f_over_w(int i, const float4 q0, const float4 q1, const float4 q2,
+                                                 const float4 q3) {
+  const int c0 = L::c(i, 0), c1 = L::c(i, 1), c2 = L::c(i, 2);
+  if (c0 == 0 && c1 == 0 && c2 == 0) return q0.x;
+  const float u0 = q0.z, u1 = q0.w, u2 = q1.x;
+  const float B00 = q2.x, B11 = q2.y, B22 = q2.z, B01 = q2.w, B02 = q3.x, B12 = q3.y;
+  // c.u, c.r, c.B.c and c.B.u with the zero components of c dropped after unrolling
+  float cu = 0.f, cr = 0.f, cbc = 0.f, cbu = 0.f;
+  if (c0) { cu += c0 * u0; cr += c0 * q1.y; cbc += B00; cbu += c0 * (B00 * u0 + B01 * u1 + B02 * u2); }
+  if (c1) { cu += c1 * u1; cr += c1 * q1.z; cbc += B11; cbu += c1 * (B01 * u0 + B11 * u1 + B12 * u2); }
+  if (c2) { cu += c2 * u2; cr += c2 * q1.w; cbc += B22; cbu += c2 * (B02 * u0 + B12 * u1 + B22 * u2); }
+  if (c0 && c1) cbc += 2.0f * c0 * c1 * B01;
+  if (c0 && c2) cbc += 2.0f * c0 * c2 * B02;
+  if (c1 && c2) cbc += 2.0f * c1 * c2 * B12;
+  const float t = 4.5f * cu;
+  const float E = q0.x + t * (cu + cr) + 4.5f * cbc;
+  const float O = cu * (q0.y + t * cu + 13.5f * cbc) - 9.0f * cbu + 1.5f * cr;
+  return E + O;
+}
+
 // ---------------------------------------------------------------------------------------------
 // phi is stored as a signed 2.30 fixed-point integer: phi = v * 2^-30. Every term of the phase
 // update is applied as an antisymmetric link transfer rounded once to this grid, so sum(phi) is

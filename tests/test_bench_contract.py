@@ -49,7 +49,7 @@ def test_repo_arm_plan_has_no_negative_step_count(argv):
         if isinstance(v, int) and not isinstance(v, bool):
             assert v >= 0, (k, v)
     assert plan["timed"] == args.steps and plan["warmup"] == args.warmup
-    assert plan["variant_stores"] == ("f16", "bf16")
+    assert plan["variant_stores"] == ("f16", "bf16", "mom")
     assert plan["early"] == bm.EARLY and plan["late"] == bm.LATE and bm.EARLY < bm.LATE
     assert plan["variant_timed"] >= 1 and plan["split_steps"] >= 1 and plan["e2e_steps"] >= 1
     assert plan["split_compare_steps"] >= 1

@@ -30,7 +30,7 @@ def test_driver_command_prints_a_complete_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] > 0
     e2e = d["e2e"]
     assert e2e["value"] > 0 and e2e["h2d_bytes_per_step"] > 0 and e2e["d2h_bytes_per_step"] > 0
-    for st in ("f16", "bf16"):
+    for st in ("f16", "bf16", "mom"):
         v = d["variants"][st]
         assert v["value"] > 0 and v["phi_mass_drift"] <= 1e-9
     o = d["vs_fp64_oracle"]
