@@ -64,6 +64,11 @@ cudaError_t phase_prepare(int dim);
 cudaError_t launch_hydro(int Q, int store, int mode, const KParams &P, const void *src, void *dst,
                          const int32_t *phi, const float4 *frep, float *u, float *pstar, cudaStream_t s);
 
+// Resident k_hydro2 blocks per SM its registers are sized for (D3Q19; D3Q27 takes 2).
+#ifndef LBM_HYDRO2_MINB
+#define LBM_HYDRO2_MINB 3
+#endif
+
 // The near-contact list of one phi buffer: the 32 x 8 x 4 tiles (3D; 32 x 8 in 2D) holding a
 // gated cell, their count, and one mark per tile of the grid (3D), set while the tile is listed.
 struct TileList {
