@@ -42,8 +42,11 @@ def nci_kernels(cfg):
 
 
 # scan blocks of the split step compared against the one-stream step (one resident block per SM
-# is 152 on a GB300)
-SPLIT_SCAN_BLOCKS = (8, 38, 152)
+# is 152 on a GB300), in alternating chunks of SPLIT_CHUNK steps
+SPLIT_SCAN_BLOCKS = (38, 76, 152)
+SPLIT_CHUNK = 25
+# the timed region records events around one hydrodynamic launch in HYDRO_SAMPLE
+HYDRO_SAMPLE = 10
 
 
 def split_applies(cfg):
@@ -277,11 +280,12 @@ def run_ours(args, world, rank, local):
     sim.step(plan["warmup"])
     sim.synchronize()
 
-    # timed region: K steps, with events on the library stream around the hydrodynamic kernel only
-    # (events around every pass would add time between kernels); the per-kernel split is taken
-    # after it, untimed
+    # timed region: K steps, with events on the library stream around the hydrodynamic kernel of one
+    # step in HYDRO_SAMPLE (events around every pass would add time between kernels); the
+    # per-kernel split is taken after it, untimed
     sampler = ClockSampler(local)
     sim.profile_kinds(["hydro"])
+    sim.profile_sample(HYDRO_SAMPLE)
     barrier(world)
     torch.cuda.synchronize()
     sampler.start()
@@ -306,29 +310,42 @@ def run_ours(args, world, rank, local):
     split = sim.profile_read()
     sim.profile(False)
 
-    # the same steps as the split step (lbm_set_overlap), for comparison: the near-contact pass and
-    # the listed tiles' hydrodynamics on a second stream, concurrent with the other tiles
+    # the split step (lbm_set_overlap) against the one-stream step over the same steps: chunks of
+    # the two alternate, so both see the same phase of the collision
     split_step = None
     if split_applies(cfg) and plan["split_compare_steps"]:
         ko = plan["split_compare_steps"]
-        split_step = {"unit": "MLUPS", "steps": ko, "one_stream_value": round(mlups / world, 1)}
-        for blocks in SPLIT_SCAN_BLOCKS:
+        chunk = min(ko, SPLIT_CHUNK)
+        split_step = {"unit": "MLUPS", "steps_each": ko, "chunk": chunk}
+
+        def timed_chunk(blocks):
             sim.set_overlap(blocks)
-            sim.step(3)
+            sim.step(2)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            sim.step(ko)
+            sim.step(chunk)
             e1.record(stream)
             e1.synchronize()
-            mo = N * ko / (e0.elapsed_time(e1) * 1e-3) / 1e6
-            split_step[f"scan_blocks_{blocks}"] = {"value": round(mo, 1), "vs_one_stream": round(mo / (mlups / world), 4)}
+            return e0.elapsed_time(e1)
+
+        for blocks in SPLIT_SCAN_BLOCKS:
+            t_one = t_split = 0.0
+            done = 0
+            while done < ko:
+                t_one += timed_chunk(0)
+                t_split += timed_chunk(blocks)
+                done += chunk
+            split_step[f"scan_blocks_{blocks}"] = {
+                "value": round(N * done / (t_split * 1e-3) / 1e6, 1),
+                "one_stream_value": round(N * done / (t_one * 1e-3) / 1e6, 1),
+                "vs_one_stream": round(t_one / t_split, 4)}
         sim.set_overlap(0)
 
     hydro_b, step_b = store_bytes_per_cell(Q, args.store)
     peak, peak_kind = measured_peaks()
-    # one hydrodynamic pass per step
-    hydro_ms, _ = prof["hydro"]
-    hydro_avg = hydro_ms / max(plan["timed"], 1)
+    # one hydrodynamic launch per sampled step (one stream)
+    hydro_ms, hydro_n = prof["hydro"]
+    hydro_avg = hydro_ms / max(hydro_n, 1)
     per_launch_bytes = hydro_b * N
     achieved = per_launch_bytes / (hydro_avg * 1e-3) / 1e9
     key = (args.store, Q, _src_hash("hydro_impl.cuh", "lbm_device.cuh"))
@@ -385,6 +402,7 @@ def run_ours(args, world, rank, local):
             s2.synchronize()
             kv = plan["variant_timed"]
             s2.profile_kinds(["hydro"])  # as in the FP32 timed region
+            s2.profile_sample(HYDRO_SAMPLE)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for _ in range(kv):
@@ -396,7 +414,8 @@ def run_ours(args, world, rank, local):
             mv1, _ = s2.mass()
             s2.close()
             msv = e0.elapsed_time(e1)
-            hm, _ = pr["hydro"]
+            hm, hn = pr["hydro"]
+            hm = hm / max(hn, 1) * kv  # the sampled mean, as a total over kv steps
             v_mlups = N * kv / (msv * 1e-3) / 1e6
             d_early = np.abs(fresh(st, plan["early"]) - ph32_early)
             ph_late = fresh(st, plan["late"])

@@ -255,6 +255,10 @@ int lbm_profile(lbm_ctx *ctx, int enable);
 /* As lbm_profile, timing only the kinds whose bit (1u << kind, kind an lbm_kernel_kind) is set in
  * mask; mask = 0 stops. Bits of kinds beyond LBM_K_COUNT are ignored. Same errors as lbm_profile. */
 int lbm_profile_kinds(lbm_ctx *ctx, unsigned mask);
+/* Times only the first and then every `every`-th pass of each profiled kind (counted from the last
+ * lbm_profile / lbm_profile_kinds call), so that a long run can be sampled with fewer events between
+ * its kernels; 1 (the default) times every pass. every < 1 or NULL ctx: LBM_ERR_ARG. */
+int lbm_profile_sample(lbm_ctx *ctx, int every);
 /* Accumulated device milliseconds and kernel launch counts per lbm_kernel_kind (arrays of
  * LBM_K_COUNT; either may be NULL). A pass of several kernels counts each of them: the near-contact
  * pass over the listed tiles is 3 kernels where the brick prefilter applies (3D, every side a

@@ -87,6 +87,7 @@ def load():
     L.lbm_synchronize.argtypes = [_VP]
     L.lbm_profile.argtypes = [_VP, ctypes.c_int]
     L.lbm_profile_kinds.argtypes = [_VP, ctypes.c_uint]
+    L.lbm_profile_sample.argtypes = [_VP, ctypes.c_int]
     L.lbm_profile_read.argtypes = [_VP, _VP, _VP]
     L.lbm_lattice.argtypes = [ctypes.c_int, ctypes.c_int, _VP, _VP]
     L.lbm_strerror.argtypes = [ctypes.c_int]
@@ -95,7 +96,7 @@ def load():
     L.lbm_kernel_name.restype = ctypes.c_char_p
     for name in ("lbm_create", "lbm_set_stream", "lbm_init_fields", "lbm_set_state", "lbm_get_state",
                  "lbm_step", "lbm_set_overlap", "lbm_get_overlap", "lbm_read_fields", "lbm_mass", "lbm_mass_noalloc", "lbm_read_nci", "lbm_synchronize",
-                 "lbm_profile", "lbm_profile_kinds", "lbm_profile_read", "lbm_lattice", "lbm_batch_create", "lbm_batch_step",
+                 "lbm_profile", "lbm_profile_kinds", "lbm_profile_sample", "lbm_profile_read", "lbm_lattice", "lbm_batch_create", "lbm_batch_step",
                  "lbm_batch_create_ex", "lbm_batch_config",
                  "lbm_nci_diagnostics", "lbm_curvature", "lbm_energy_spectrum",
                  "lbm_batch_synchronize"):
@@ -282,6 +283,10 @@ def lbm_profile_kinds(ctx: int, kinds) -> None:
     _check(load().lbm_profile_kinds(_VP(ctx), mask), "lbm_profile_kinds")
 
 
+def lbm_profile_sample(ctx: int, every: int) -> None:
+    _check(load().lbm_profile_sample(_VP(ctx), int(every)), "lbm_profile_sample")
+
+
 def lbm_profile_read(ctx: int):
     ms = np.zeros(len(KERNEL_KINDS))
     n = np.zeros(len(KERNEL_KINDS), dtype=np.int64)
@@ -445,6 +450,9 @@ class Lbm:
 
     def profile_kinds(self, kinds):
         lbm_profile_kinds(self.ctx, kinds)
+
+    def profile_sample(self, every: int):
+        lbm_profile_sample(self.ctx, every)
 
     def profile_read(self):
         return lbm_profile_read(self.ctx)

@@ -57,6 +57,8 @@ struct lbm_ctx {
   std::vector<cudaEvent_t> pool;
   double prof_ms[LBM_K_COUNT] = {0};
   int64_t prof_n[LBM_K_COUNT] = {0};
+  int64_t prof_seen[LBM_K_COUNT] = {0};  // passes of each kind since the profiler was (re)started
+  int prof_every = 1;                    // time one pass in every prof_every of each kind
 };
 
 // The near-contact list of phi buffer k.

@@ -47,6 +47,7 @@ cudaEvent_t take_event(lbm_ctx *c) {
 // profiler is on.
 template <class F> cudaError_t timed_on(lbm_ctx *c, cudaStream_t s, int kind, F &&launch, int kernels = 1) {
   if (!c->prof || !((c->prof_mask >> kind) & 1u)) return launch();
+  if (c->prof_seen[kind]++ % c->prof_every != 0) return launch();  // a pass between samples
   cudaEvent_t a = take_event(c), b = take_event(c);
   if (!a || !b) return cudaErrorMemoryAllocation;
   cudaEventRecord(a, s);
@@ -640,9 +641,16 @@ int lbm_profile_kinds(lbm_ctx *c, unsigned mask) {
   for (int k = 0; k < LBM_K_COUNT; k++) {
     c->prof_ms[k] = 0;
     c->prof_n[k] = 0;
+    c->prof_seen[k] = 0;
   }
   c->prof_mask = mask & ((1u << LBM_K_COUNT) - 1u);
   c->prof = c->prof_mask != 0;
+  return LBM_OK;
+}
+
+int lbm_profile_sample(lbm_ctx *c, int every) {
+  if (!c || every < 1) return LBM_ERR_ARG;
+  c->prof_every = every;
   return LBM_OK;
 }
 

@@ -71,6 +71,36 @@ def test_batch_matches_per_case_steps(nstreams):
         s.close()
 
 
+@pytest.mark.parametrize("flags", [1, 0])
+def test_batch_of_split_step_contexts(flags):
+    """Contexts running the split step (lbm_set_overlap) in a batch: the per-case graph (flags 1)
+    captures their two-stream steps, the fused mode their odd plain steps; both bit-equal to
+    one-stream per-case steps."""
+    cases = _small_cases()
+    single, batched = [], []
+    for cfg in cases:
+        phi, u = W.sweep_case_fields(cfg)
+        for lst in (single, batched):
+            s = B.Lbm(cfg)
+            s.init_fields(phi, u)
+            lst.append(s)
+        split = cfg["dim"] == 3 and cfg["nci_on"] and cfg["nx"] % 2 == 0
+        if split:
+            batched[-1].set_overlap(8)
+        assert batched[-1].overlap() == (8 if split else 0)
+    assert sum(s.overlap() > 0 for s in batched) >= 3
+    batch = B.LbmBatch(batched, nstreams=3, flags=flags)
+    for n in (4, 3, 1, 2):
+        batch.step(n)
+        for s in single:
+            s.step(n)
+        for a, b in zip(_states(single), _states(batched)):
+            assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    batch.close()
+    for s in single + batched:
+        s.close()
+
+
 def _uniform_3d_cases(Q=19):
     """Uneven 3D cases of one lattice (x sides even), near-contact on and off: the fused batch."""
     cases = []

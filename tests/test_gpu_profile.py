@@ -41,4 +41,11 @@ def test_profile_kinds_and_counts(dims, nci_kernels, hydro_kernels, overlap):
     sim.profile_kinds([])
     sim.step(1)
     assert sim.profile_read()["hydro"] == (0.0, 0)
+    # sampling: the first pass and every third after it (passes 0, 3, 6 of 7)
+    sim.profile_kinds(["hydro", "phase"])
+    sim.profile_sample(3)
+    sim.step(7)
+    p = sim.profile_read()
+    assert p["hydro"][1] == 3 * hydro_kernels and p["phase"][1] == 3 and p["hydro"][0] > 0
+    sim.profile_sample(1)
     sim.close()
