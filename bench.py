@@ -87,9 +87,9 @@ def store_bytes_per_cell(Q, store):
 # profiles/ (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hydro kernel source hash:
 # a changed kernel reports null until it is profiled again.
 HYDRO_TRAFFIC = {
-    # 337.55 MB read + 321.63 MB written (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,
+    # 337.76 MB read + 323.17 MB written (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,
     # one step launch of k_hydro2 on the 256x128x128 case; profiles/launches_collision_256x128x128.md)
-    ("f32", 19, "565b194baca8287c"): 659.19e6,
+    ("f32", 19, "86bb24acb2461a5c"): 660.93e6,
 }
 
 
@@ -250,7 +250,7 @@ def run_plan(args, world, rank):
     return {
         "warmup": max(args.warmup, 0), "timed": max(args.steps, 0),
         "split_steps": max(min(args.steps, 500), 1),
-        "split_compare_steps": max(min(args.steps, 500), 1),
+        "split_compare_steps": max(min(args.steps, 500), 1) if args.split_compare else 0,
         "e2e_steps": max(args.steps, 1) if not args.no_e2e else 0,
         "variant_stores": ("f16", "bf16", "mom") if variants else (),
         "variant_timed": max(args.steps, 1), "early": EARLY, "late": LATE,
@@ -924,6 +924,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", dest="variants", action="store_false")
+    ap.add_argument("--no-split-compare", dest="split_compare", action="store_false",
+                    help="skip the split-step comparison (profiling runs)")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=120.0, help="seconds for the whole reference arm")
     ap.add_argument("--workload", choices=["collision", "sweep", "swarm", "selftune", "impact"], default="collision",

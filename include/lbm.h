@@ -215,7 +215,8 @@ int lbm_batch_create(lbm_ctx *const *ctxs, int n, int nstreams, void *stream, lb
  * identical. An autotuner then times, on the contexts' own state and without changing it, the
  * hydrodynamic tile shape (64 x ty x 8/ty cells, ty = 4, 2, 8) and the rows of y per thread of the
  * phase-field march (4 or 2), keeps the fastest, and finally times one step of that fused
- * execution against one step of the per-case graph and keeps the faster (lbm_batch_config).
+ * execution against one step of the per-case graph, keeping the fused execution only when it is at
+ * least 3 % faster (lbm_batch_config reports both times).
  * Otherwise, or with LBM_BATCH_PER_CASE, the graph holds every context's own steps on the branches.
  * LBM_BATCH_NO_TUNE keeps ty = 4 and 4 rows; LBM_BATCH_HYDRO_TY2 / _TY8 and LBM_BATCH_PHASE_ROWS2
  * pin those choices instead (no tuning). Creation allocates the work lists (8 B per tile) and a

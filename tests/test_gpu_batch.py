@@ -137,7 +137,7 @@ def test_fused_batch_matches_per_case_steps(Q, store, flags):
     else:
         t = cfg["tune_ms"]
         assert all(v > 0 for v in t.values())
-        assert cfg["fused"] == (1 if t["step_fused"] <= t["step_per_case"] else 0)
+        assert cfg["fused"] == (1 if t["step_fused"] < 0.97 * t["step_per_case"] else 0)
     for n in (4, 3, 0, 1, 3, 2, 1, 6):
         batch.step(n)
         for s in single:
