@@ -305,6 +305,7 @@ def run_ours(args, world, rank, local):
     mlups, ms_max = whole_job_mlups(world, N, args.steps, ms_total, device=f"cuda:{local}")
     m1, _ = sim.mass()
     split_steps = plan["split_steps"]
+    sim.profile_sample(1)  # every pass of the untimed split
     sim.profile(True)
     sim.step(split_steps)
     split = sim.profile_read()

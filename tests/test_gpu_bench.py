@@ -36,6 +36,10 @@ def test_driver_command_prints_a_complete_line():
     o = d["vs_fp64_oracle"]
     assert o["steps"] >= 1 and o["f32"]["max_dphi"] <= 1e-5 and o["f32"]["max_du"] <= 1e-6
     assert d["gpu_launches"] == 5 * 20
+    # the untimed per-kernel split times every pass: the passes add up to about a step
+    ks = d["kernels_ms_per_step"]
+    assert 0.8 * d["ms_per_step"] <= ks["nci"] + ks["hydro"] + ks["phase"] <= 1.5 * d["ms_per_step"]
+    assert abs(ks["hydro"] - rf["avg_ms"]) <= 0.2 * rf["avg_ms"]
     sp = d["split_step"]
     assert all(sp[f"scan_blocks_{b}"]["value"] > 0 and sp[f"scan_blocks_{b}"]["one_stream_value"] > 0
                for b in (38, 76, 152))
