@@ -91,21 +91,22 @@ __device__ __forceinline__ long long cell_shift(const KParams &P, int x, int y, 
 }
 
 // Initial populations f_eq(p*, u) (Eq. 11, evaluated in FP64), stored for the pull scheme:
-// buffer cell y holds the population that streams to y + c_i, i.e. f_eq_i at y + c_i.
+// buffer cell y holds the population that streams to y + c_i, i.e. f_eq_i at y + c_i. The thread of
+// cell m evaluates its own f_eq_i and writes it to m - c_i (each cell's fields are read once).
 template <class L, int S>
 __global__ void k_init_pops(const KParams P, const double *__restrict__ u64, const double *__restrict__ ps64,
                             typename Store<S>::T *__restrict__ pops) {
-  long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n >= P.N) return;
-  int x = (int)(n % P.nx), y = (int)((n / P.nx) % P.ny), z = (int)(n / ((long long)P.nx * P.ny));
+  long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (m >= P.N) return;
+  int x = (int)(m % P.nx), y = (int)((m / P.nx) % P.ny), z = (int)(m / ((long long)P.nx * P.ny));
+  const double u0 = u64[m], u1 = u64[P.N + m], u2 = L::D == 3 ? u64[2 * P.N + m] : 0.0;
+  const double ps = ps64 ? ps64[m] : 0.0;
+  const double uu = u0 * u0 + u1 * u1 + u2 * u2;
 #pragma unroll
   for (int i = 0; i < L::Q; i++) {
-    long long m = cell_shift(P, x, y, z, L::c(i, 0), L::c(i, 1), L::c(i, 2), L::D);
-    double u0 = u64[m], u1 = u64[P.N + m], u2 = L::D == 3 ? u64[2 * P.N + m] : 0.0;
-    double ps = ps64 ? ps64[m] : 0.0;
-    double cu = L::c(i, 0) * u0 + L::c(i, 1) * u1 + L::c(i, 2) * u2;
-    double uu = u0 * u0 + u1 * u1 + u2 * u2;
-    double feq = L::wd(i) * (ps + 3.0 * cu + 4.5 * (cu * cu - uu / 3.0) + 4.5 * (cu * cu * cu - uu * cu));
+    const long long n = cell_shift(P, x, y, z, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2), L::D);
+    const double cu = L::c(i, 0) * u0 + L::c(i, 1) * u1 + L::c(i, 2) * u2;
+    const double feq = L::wd(i) * (ps + 3.0 * cu + 4.5 * (cu * cu - uu / 3.0) + 4.5 * (cu * cu * cu - uu * cu));
     Store<S>::st(pops + (long long)i * P.N + n, (float)feq, L::w(i));
   }
 }
