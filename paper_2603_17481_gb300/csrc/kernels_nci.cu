@@ -677,7 +677,8 @@ static cudaError_t launch_nci_dim(const KParams &P, const NciTable &T, const int
   if (e != cudaSuccess) return e;
   const int gtx = (P.nx + G::TX - 1) / G::TX, gty = (P.ny + G::TY - 1) / G::TY, gtz = (P.nz + G::TZ - 1) / G::TZ;
   const int total = gtx * gty * gtz;
-  const int blocks = tiles ? list_blocks : (total < list_blocks * 4 ? total : list_blocks * 4);
+  // resident blocks walk the list; a small grid has fewer tiles than that
+  const int blocks = tiles ? (total < list_blocks ? total : list_blocks) : (total < list_blocks * 4 ? total : list_blocks * 4);
   dim3 block(G::TX, G::TY, G::TZ);
   const bool pre = DIM == 3 && aux && tiles && aux->bricks && nci_aux_applies(DIM, P);
   const NciAux none{};
@@ -696,7 +697,8 @@ static cudaError_t launch_nci_dim(const KParams &P, const NciTable &T, const int
     return launch_pdl(k_nci_scan<DIM>, dim3(blocks), block, G::smem, s, P, T, phi, nrm, frep, partner, debug, tiles,
                       ntiles, total, gtx, gty, nullptr, nullptr, nullptr);
   }
-  e = launch_pdl(k_nci_prefilter, dim3(16 * list_blocks), dim3(128), 0, s, P, (const uint4 *)aux->bricks,
+  e = launch_pdl(k_nci_prefilter, dim3(total < 16 * list_blocks ? total : 16 * list_blocks), dim3(128), 0, s, P,
+                 (const uint4 *)aux->bricks,
                  (const unsigned char *)aux->flags, tiles, ntiles, aux->scan_tiles, aux->nscan, gtx, gty);
   if (e != cudaSuccess) return e;
   return launch_pdl(k_nci_scan<DIM>, dim3(blocks), block, G::smem, s, P, T, phi, nrm, frep, partner, debug,
