@@ -314,7 +314,7 @@ def run_ours(args, world, rank, local):
     # the split step (lbm_set_overlap) against the one-stream step over the same steps: chunks of
     # the two alternate, so both see the same phase of the collision
     split_step = None
-    if split_applies(cfg) and plan["split_compare_steps"]:
+    if split_applies(cfg) and args.store != "mom" and plan["split_compare_steps"]:  # populations only
         ko = plan["split_compare_steps"]
         chunk = min(ko, SPLIT_CHUNK)
         split_step = {"unit": "MLUPS", "steps_each": ko, "chunk": chunk}

@@ -43,3 +43,17 @@ def test_driver_command_prints_a_complete_line():
     sp = d["split_step"]
     assert all(sp[f"scan_blocks_{b}"]["value"] > 0 and sp[f"scan_blocks_{b}"]["one_stream_value"] > 0
                for b in (38, 76, 152))
+
+
+@pytest.mark.parametrize("extra", [["--store", "f16"], ["--store", "mom"], ["--lattice", "27"]])
+def test_other_stores_and_lattices_print_a_line(extra):
+    """The bench's other population stores and the D3Q27 lattice run through the same timed path."""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--steps", "5", "--warmup", "3", "--no-e2e",
+                        "--no-cpu-baseline", "--no-variants", *extra], capture_output=True, text=True, timeout=900, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-3000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["value"] > 0 and d["roofline"]["frac"] > 0
+    if extra[1] == "mom":
+        assert d["split_step"] is None and d["roofline"]["bytes_per_cell"] == 144
