@@ -258,12 +258,15 @@ int lbm_profile(lbm_ctx *ctx, int enable);
 int lbm_profile_kinds(lbm_ctx *ctx, unsigned mask);
 /* Times only the first and then every `every`-th pass of each profiled kind (counted from the last
  * lbm_profile / lbm_profile_kinds call), so that a long run can be sampled with fewer events between
- * its kernels; 1 (the default) times every pass. every < 1 or NULL ctx: LBM_ERR_ARG. */
+ * its kernels; 1 (the default) times every pass. The setting stays until changed. every < 1 or NULL
+ * ctx: LBM_ERR_ARG. */
 int lbm_profile_sample(lbm_ctx *ctx, int every);
 /* Accumulated device milliseconds and kernel launch counts per lbm_kernel_kind (arrays of
  * LBM_K_COUNT; either may be NULL). A pass of several kernels counts each of them: the near-contact
  * pass over the listed tiles is 3 kernels where the brick prefilter applies (3D, every side a
- * multiple of 4) and 2 elsewhere; a reduction is 2. Synchronises the stream. */
+ * multiple of 4) and 2 elsewhere; a reduction is 2; the split step's hydrodynamic pass is 2, timed
+ * from its first launch to the join of both (the concurrent near-contact pass runs inside that time).
+ * Synchronises the stream. */
 int lbm_profile_read(lbm_ctx *ctx, double *ms, int64_t *launches);
 
 /* Velocity table of a hydrodynamic lattice in the order above: c is 3*Q ints, w is Q doubles. */
