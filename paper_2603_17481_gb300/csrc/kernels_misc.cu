@@ -90,24 +90,43 @@ __device__ __forceinline__ long long cell_shift(const KParams &P, int x, int y, 
   return (long long)X + (long long)P.nx * (Y + (long long)P.ny * Z);
 }
 
-// Initial populations f_eq(p*, u) (Eq. 11, evaluated in FP64), stored for the pull scheme:
-// buffer cell y holds the population that streams to y + c_i, i.e. f_eq_i at y + c_i. The thread of
-// cell m evaluates its own f_eq_i and writes it to m - c_i (each cell's fields are read once).
+// Initial populations f_eq(p*, u) (Eq. 11), stored for the pull scheme: buffer cell y holds the
+// population that streams to y + c_i, i.e. f_eq_i at y + c_i. The thread of cell m evaluates its
+// own f_eq_i and writes it to m - c_i (each cell's fields are read once). The equilibrium is
+// evaluated in FP32, the precision of every later update, in its even / odd split over the pair
+// (c, -c): with A = p* - 1.5 |u|^2 and B = 3 - 4.5 |u|^2,
+//   f_eq(+-c) / w = E +- O,  E = A + 4.5 (c.u)^2,  O = (c.u)(B + 4.5 (c.u)^2),
+// which is the third-order polynomial of Eq. 11 regrouped (cs^2 = 1/3); each c.u is a sum of
+// signed velocity components. GB300 runs FP64 at a small fraction of its FP32 rate: the same
+// polynomial in FP64 took as long as seven time steps of the grid.
 template <class L, int S>
 __global__ void k_init_pops(const KParams P, const double *__restrict__ u64, const double *__restrict__ ps64,
                             typename Store<S>::T *__restrict__ pops) {
   long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (m >= P.N) return;
   int x = (int)(m % P.nx), y = (int)((m / P.nx) % P.ny), z = (int)(m / ((long long)P.nx * P.ny));
-  const double u0 = u64[m], u1 = u64[P.N + m], u2 = L::D == 3 ? u64[2 * P.N + m] : 0.0;
-  const double ps = ps64 ? ps64[m] : 0.0;
-  const double uu = u0 * u0 + u1 * u1 + u2 * u2;
-#pragma unroll
-  for (int i = 0; i < L::Q; i++) {
+  const float u[3] = {(float)u64[m], (float)u64[P.N + m], L::D == 3 ? (float)u64[2 * P.N + m] : 0.0f};
+  const float ps = ps64 ? (float)ps64[m] : 0.0f;
+  const float uu = __fmaf_rn(u[0], u[0], __fmaf_rn(u[1], u[1], __fmul_rn(u[2], u[2])));
+  const float A = __fmaf_rn(-1.5f, uu, ps), B = __fmaf_rn(-4.5f, uu, 3.0f);
+  auto put = [&](int i, float g) {
     const long long n = cell_shift(P, x, y, z, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2), L::D);
-    const double cu = L::c(i, 0) * u0 + L::c(i, 1) * u1 + L::c(i, 2) * u2;
-    const double feq = L::wd(i) * (ps + 3.0 * cu + 4.5 * (cu * cu - uu / 3.0) + 4.5 * (cu * cu * cu - uu * cu));
-    Store<S>::st(pops + (long long)i * P.N + n, (float)feq, L::w(i));
+    Store<S>::st_w(pops + (long long)i * P.N + n, g, L::w(i));
+  };
+  put(0, A);
+#pragma unroll
+  for (int i = 1; i < L::Q; i++) {
+    if (L::opp(i) < i) continue;  // each pair once, through its lower index
+    float cu = 0.0f;
+#pragma unroll
+    for (int a = 0; a < L::D; a++) {
+      if (L::c(i, a) > 0) cu = __fadd_rn(cu, u[a]);
+      if (L::c(i, a) < 0) cu = __fsub_rn(cu, u[a]);
+    }
+    const float s = __fmul_rn(cu, cu);
+    const float E = __fmaf_rn(4.5f, s, A), O = __fmul_rn(cu, __fmaf_rn(4.5f, s, B));
+    put(i, __fadd_rn(E, O));
+    put(L::opp(i), __fsub_rn(E, O));
   }
 }
 
@@ -242,6 +261,9 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
 
 constexpr int kReduceThreads = 256;
 
+// MOM = false leaves out the FP64 momentum sums (GB300's FP64 rate makes them the cost of this
+// kernel): the phi sum and, when u is given, the non-finite count only.
+template <bool MOM>
 __global__ void __launch_bounds__(kReduceThreads)
 k_reduce_partial(const KParams P, const int32_t *__restrict__ phi, const float *__restrict__ u,
                  ReduceOut *__restrict__ partials) {
@@ -251,12 +273,15 @@ k_reduce_partial(const KParams P, const int32_t *__restrict__ phi, const float *
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < P.N; n += stride) {
     const int32_t v = phi[n];
     sphi += v;
-    const double rho = P.rho_g64 + P.drho64 * ((double)v * (1.0 / 1073741824.0));
+    if (!MOM && !u) continue;
     const float a = u[n], b = u[P.N + n], c = u[2 * P.N + n];
     if (!isfinite(a) || !isfinite(b) || !isfinite(c)) nonfin++;
-    m0 += rho * a;
-    m1 += rho * b;
-    m2 += rho * c;
+    if constexpr (MOM) {
+      const double rho = P.rho_g64 + P.drho64 * ((double)v * (1.0 / 1073741824.0));
+      m0 += rho * a;
+      m1 += rho * b;
+      m2 += rho * c;
+    }
   }
   __shared__ double sm[3][kReduceThreads / 32];
   __shared__ long long sl[2][kReduceThreads / 32];
@@ -304,14 +329,15 @@ __global__ void k_reduce_final(const ReduceOut *__restrict__ partials, int n, Re
 
 cudaError_t launch_reduce_n(const KParams &P, const int32_t *phi, const float *u, ReduceOut *partials, int nblocks,
                             ReduceOut *out, cudaStream_t s) {
-  k_reduce_partial<<<nblocks, kReduceThreads, 0, s>>>(P, phi, u, partials);
+  k_reduce_partial<true><<<nblocks, kReduceThreads, 0, s>>>(P, phi, u, partials);
   k_reduce_final<<<1, 32, 0, s>>>(partials, nblocks, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_reduce(const KParams &P, const int32_t *phi, const float *u, ReduceOut *partials, ReduceOut *out,
-                          cudaStream_t s) {
-  k_reduce_partial<<<kReduceBlocks, kReduceThreads, 0, s>>>(P, phi, u, partials);
+                          cudaStream_t s, bool mom) {
+  if (mom) k_reduce_partial<true><<<kReduceBlocks, kReduceThreads, 0, s>>>(P, phi, u, partials);
+  else k_reduce_partial<false><<<kReduceBlocks, kReduceThreads, 0, s>>>(P, phi, u, partials);
   k_reduce_final<<<1, 32, 0, s>>>(partials, kReduceBlocks, out);
   return cudaGetLastError();
 }

@@ -151,8 +151,10 @@ struct ReduceOut {
   long long nonfinite;
 };
 constexpr int kReduceBlocks = 608;  // 4 per SM of a 152-SM GB300
+// The phi sum (exact), the non-finite count of u (u may be null when mom is false) and, with mom,
+// the FP64 momentum sum of rho(phi) u.
 cudaError_t launch_reduce(const KParams &P, const int32_t *phi, const float *u, ReduceOut *partials,
-                          ReduceOut *out, cudaStream_t s);
+                          ReduceOut *out, cudaStream_t s, bool mom = true);
 // The same reduction on a grid of nblocks blocks (nblocks partial slots).
 cudaError_t launch_reduce_n(const KParams &P, const int32_t *phi, const float *u, ReduceOut *partials,
                             int nblocks, ReduceOut *out, cudaStream_t s);

@@ -176,7 +176,7 @@ int finish_init(lbm_ctx *c) {
   if (rc) return rc;
   rc = from_cuda(launch_gate_tiles(c->P.dim, c->K, c->phi[c->pcur], tile_list(c, c->pcur), c->stream));
   if (rc) return rc;
-  rc = from_cuda(launch_reduce(c->K, c->phi[c->pcur], c->u, c->red_part, c->red_out, c->stream));
+  rc = from_cuda(launch_reduce(c->K, c->phi[c->pcur], nullptr, c->red_part, c->red_out, c->stream, false));
   if (rc) return rc;
   ReduceOut r;
   if ((rc = d2h(c, &r, c->red_out, sizeof(r)))) return rc;
@@ -460,7 +460,7 @@ int lbm_step(lbm_ctx *c, int n) {
     c->steps++;
     if (c->P.mass_check_every > 0 && c->steps % c->P.mass_check_every == 0) {
       rc = from_cuda(timed(c, LBM_K_REDUCE, [&] {
-        return launch_reduce(c->K, c->phi[c->pcur], c->u, c->red_part, c->red_out, c->stream);
+        return launch_reduce(c->K, c->phi[c->pcur], c->u, c->red_part, c->red_out, c->stream, false);
       }, 2));
       if (rc) return rc;
       ReduceOut r;

@@ -58,6 +58,41 @@ CASES_1STEP = [
 ]
 
 
+@pytest.mark.parametrize("dim,Q,shape", [(3, 19, (37, 21, 13)), (3, 27, (35, 19, 11)), (2, 9, (45, 27, 1))])
+@pytest.mark.parametrize("store", ["f32", "f16", "bf16"])
+def test_initial_populations_are_the_equilibrium(dim, Q, shape, store):
+    """lbm_init_fields sets f_eq(p*, u) of Eq. 11 (evaluated in FP32): every population within a few
+    FP32 units of the oracle's FP64 equilibrium (FP32 store), or within one unit of the storage
+    precision of f / w (FP16, BF16). A dropped term (the cubic 4.5 (c.u)^3 is above 1e-5 here) or a
+    swapped direction fails by orders of magnitude."""
+    cfg = W.base_config(dim, *shape, Q, rho_g=0.1)
+    phi, u = W.smooth_random_fields(cfg, seed=29)
+    phi = W.to_q30_grid(phi)
+    u = 3.0 * u  # |u| up to about 0.1, so every term of the polynomial is well above FP32 rounding
+    N = W.ncells(cfg)
+    ps = W.noise(N, 30, 5e-3)
+    P = O.make_params(cfg)
+    fo = O.init(P, phi, u, pstar=ps)
+    c, w = O.lattice(dim, Q)
+    sim = B.Lbm(cfg, store=store)
+    sim.init_fields(phi, u, ps)
+    fg, phg = sim.get_state()
+    sim.close()
+    assert np.array_equal(phg, phi)
+    go, gg = fo / w[:, None], fg / w[:, None]
+    c = np.asarray(c, dtype=np.float64)
+    assert np.max(np.abs(c @ u)) > 0.05
+    if store == "f32":
+        # FP32 rounding scales with sum_a |c_a u_a| (the sum c.u may cancel), with |p*| and |u|^2
+        cabs = np.abs(c) @ np.abs(u)
+        scale = np.abs(ps)[None, :] + 3.0 * cabs + 4.5 * cabs ** 2 + 1.5 * np.sum(u * u, axis=0)[None, :] + 1e-3
+        err = np.abs(gg - go) / scale
+        assert np.max(err) <= 8 * 2.0 ** -24, f"max error {np.max(err):.3e} of the term scale"
+    else:
+        ulp = 2.0 ** -10 if store == "f16" else 2.0 ** -7
+        assert np.all(np.abs(gg - go) <= ulp * np.abs(go) + 2.0 ** -24)
+
+
 @pytest.mark.parametrize("dim,Q,shape,seed,store", CASES_1STEP)
 def test_single_step_identical_input(dim, Q, shape, seed, store):
     """One step from a random non-equilibrium state with two nearly touching droplets: near-contact
