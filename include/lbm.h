@@ -105,8 +105,15 @@ void lbm_destroy(lbm_ctx *ctx);
  * still return only after their work is complete, except lbm_step (see below). */
 int lbm_set_stream(lbm_ctx *ctx, void *stream);
 
+/* Host arrays of lbm_init_fields and lbm_read_fields: an array that lies in page-locked host
+ * memory (cudaHostAlloc, cudaHostRegister; e.g. a pinned torch tensor, or a view into one) is read
+ * or written in place by the conversion kernels over the host link; any other host array goes
+ * through a device staging buffer (5 N doubles, allocated on first use and kept) with one copy.
+ * Either way the call returns only after its last access to the caller's arrays. */
+
 /* Initial state: phi (N), u (3N) and p* (N, or NULL for p* = 0) on the host. Populations become
- * the third-order equilibrium f_eq(p*, u) (Eq. 11); rho_bar is the mean of rho(phi). */
+ * the third-order equilibrium f_eq(p*, u) (Eq. 11, evaluated in FP32); rho_bar is the mean of
+ * rho(phi). */
 int lbm_init_fields(lbm_ctx *ctx, const double *phi, const double *u, const double *pstar);
 
 /* Full state: pre-collision populations f (Q*N) and phi (N). rho_bar becomes the mean rho(phi). */

@@ -167,6 +167,28 @@ int d2h(lbm_ctx *c, void *dst, const void *src, size_t bytes) {
 }
 int sync(lbm_ctx *c) { return from_cuda(cudaStreamSynchronize(c->stream)); }
 
+// Device address of a caller's host array of `bytes` bytes when the whole array lies in one
+// page-locked host allocation (cudaHostAlloc, cudaHostRegister): such memory is mapped into the
+// device's address space, so the conversion kernels read or write it in place over the host link
+// and the conversion hides under the transfer (the copy engines and the SMs reach the same link
+// bandwidth). Null for any other memory, which goes through the staging buffer with one copy.
+template <class T>
+T *mapped_view(T *p, size_t bytes) {
+  if (!p || bytes == 0) return nullptr;
+  const char *lo = reinterpret_cast<const char *>(p), *hi = lo + bytes - 1;
+  cudaPointerAttributes a{}, b{};
+  if (cudaPointerGetAttributes(&a, lo) != cudaSuccess || cudaPointerGetAttributes(&b, hi) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer || !b.devicePointer)
+    return nullptr;
+  // both ends map into one contiguous device range (one allocation, no gap)
+  if (static_cast<const char *>(b.devicePointer) - static_cast<const char *>(a.devicePointer) != (ptrdiff_t)(bytes - 1))
+    return nullptr;
+  return static_cast<T *>(a.devicePointer);
+}
+
 // rho_bar from the exact phi sum; also records the phi-mass reference of the conservation check
 // and lists the near-contact tiles of the initial phi.
 int finish_init(lbm_ctx *c) {
@@ -378,18 +400,29 @@ int lbm_set_stream(lbm_ctx *c, void *stream) {
 int lbm_init_fields(lbm_ctx *c, const double *phi, const double *u, const double *pstar) {
   if (!c || !phi || !u) return LBM_ERR_ARG;
   const long long N = c->N;
-  int rc = ensure_stage(c, sizeof(double) * 5 * N);
-  if (rc) return rc;
-  double *s_phi = c->stage, *s_u = c->stage + N, *s_ps = c->stage + 4 * N;
-  if ((rc = h2d(c, s_phi, phi, sizeof(double) * N))) return rc;
-  if ((rc = h2d(c, s_u, u, sizeof(double) * 3 * N))) return rc;
-  if (pstar && (rc = h2d(c, s_ps, pstar, sizeof(double) * N))) return rc;
+  const size_t bN = sizeof(double) * N;
+  // page-locked inputs are read in place; the others are staged
+  const double *d_phi = mapped_view(phi, bN), *d_u = mapped_view(u, 3 * bN), *d_ps = mapped_view(pstar, bN);
+  int rc = LBM_OK;
+  if ((!d_phi || !d_u || (pstar && !d_ps)) && (rc = ensure_stage(c, 5 * bN))) return rc;
+  if (!d_phi) {
+    if ((rc = h2d(c, c->stage, phi, bN))) return rc;
+    d_phi = c->stage;
+  }
+  if (!d_u) {
+    if ((rc = h2d(c, c->stage + N, u, 3 * bN))) return rc;
+    d_u = c->stage + N;
+  }
+  if (pstar && !d_ps) {
+    if ((rc = h2d(c, c->stage + 4 * N, pstar, bN))) return rc;
+    d_ps = c->stage + 4 * N;
+  }
   c->cur = 0;
   c->pcur = 0;
-  rc = from_cuda(timed(c, LBM_K_CONVERT, [&] { return launch_phi_in(c->K, s_phi, c->phi[0], c->stream); }));
+  rc = from_cuda(timed(c, LBM_K_CONVERT, [&] { return launch_phi_in(c->K, d_phi, c->phi[0], c->stream); }));
   if (rc) return rc;
   rc = from_cuda(timed(c, LBM_K_CONVERT, [&] {
-    return launch_init_pops(c->P.Q, c->P.store, c->K, s_u, pstar ? s_ps : nullptr, c->pop[0], c->stream);
+    return launch_init_pops(c->P.Q, c->P.store, c->K, d_u, d_ps, c->pop[0], c->stream);
   }));
   if (rc) return rc;
   return finish_init(c);
@@ -478,25 +511,31 @@ int lbm_read_fields(lbm_ctx *c, double *phi, double *u, double *pstar) {
   if (!c) return LBM_ERR_ARG;
   if (!c->initialised) return LBM_ERR_STATE;
   const long long N = c->N;
-  int rc = ensure_stage(c, sizeof(double) * 5 * N);
-  if (rc) return rc;
+  const size_t bN = sizeof(double) * N;
+  // page-locked outputs are written in place; the others are staged
+  double *o_phi = mapped_view(phi, bN), *o_u = mapped_view(u, 3 * bN), *o_ps = mapped_view(pstar, bN);
+  int rc = LBM_OK;
+  if (((phi && !o_phi) || (u && !o_u) || (pstar && !o_ps)) && (rc = ensure_stage(c, 5 * bN))) return rc;
   if (u || pstar) {
     if ((rc = run_moments(c))) return rc;
   }
   if (phi) {
-    rc = from_cuda(timed(c, LBM_K_CONVERT, [&] { return launch_phi_out(c->K, c->phi[c->pcur], c->stage, c->stream); }));
+    double *t = o_phi ? o_phi : c->stage;
+    rc = from_cuda(timed(c, LBM_K_CONVERT, [&] { return launch_phi_out(c->K, c->phi[c->pcur], t, c->stream); }));
     if (rc) return rc;
-    if ((rc = d2h(c, phi, c->stage, sizeof(double) * N))) return rc;
+    if (!o_phi && (rc = d2h(c, phi, t, bN))) return rc;
   }
   if (u) {
-    rc = from_cuda(timed(c, LBM_K_CONVERT, [&] { return launch_f32_out(3 * N, c->mom, c->stage + N, c->stream); }));
+    double *t = o_u ? o_u : c->stage + N;
+    rc = from_cuda(timed(c, LBM_K_CONVERT, [&] { return launch_f32_out(3 * N, c->mom, t, c->stream); }));
     if (rc) return rc;
-    if ((rc = d2h(c, u, c->stage + N, sizeof(double) * 3 * N))) return rc;
+    if (!o_u && (rc = d2h(c, u, t, 3 * bN))) return rc;
   }
   if (pstar) {
-    rc = from_cuda(timed(c, LBM_K_CONVERT, [&] { return launch_f32_out(N, c->mom + 3 * N, c->stage + 4 * N, c->stream); }));
+    double *t = o_ps ? o_ps : c->stage + 4 * N;
+    rc = from_cuda(timed(c, LBM_K_CONVERT, [&] { return launch_f32_out(N, c->mom + 3 * N, t, c->stream); }));
     if (rc) return rc;
-    if ((rc = d2h(c, pstar, c->stage + 4 * N, sizeof(double) * N))) return rc;
+    if (!o_ps && (rc = d2h(c, pstar, t, bN))) return rc;
   }
   return sync(c);
 }
