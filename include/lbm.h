@@ -109,7 +109,9 @@ int lbm_set_stream(lbm_ctx *ctx, void *stream);
  * memory (cudaHostAlloc, cudaHostRegister; e.g. a pinned torch tensor, or a view into one) is read
  * or written in place by the conversion kernels over the host link; any other host array goes
  * through a device staging buffer (5 N doubles, allocated on first use and kept) with one copy.
- * Either way the call returns only after its last access to the caller's arrays. */
+ * An output in memory the device may only read (cudaHostRegisterReadOnly) is not stored to by a
+ * kernel: it takes the staging route. Either way the call returns only after its last access to
+ * the caller's arrays. */
 
 /* Initial state: phi (N), u (3N) and p* (N, or NULL for p* = 0) on the host. Populations become
  * the third-order equilibrium f_eq(p*, u) (Eq. 11, evaluated in FP32); rho_bar is the mean of

@@ -12,6 +12,8 @@
 //   tiles[2] int          near-contact tiles holding an interfacial cell of phi[k] (+ 2 counts)
 //   lflag    2 x int      per near-contact tile and phi buffer: the tile is in that buffer's list
 //   red      reduction partials and result
+#include <cuda.h>  // driver API types (CUpointer_attribute); no driver symbols are linked
+
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -172,8 +174,31 @@ int sync(lbm_ctx *c) { return from_cuda(cudaStreamSynchronize(c->stream)); }
 // device's address space, so the conversion kernels read or write it in place over the host link
 // and the conversion hides under the transfer (the copy engines and the SMs reach the same link
 // bandwidth). Null for any other memory, which goes through the staging buffer with one copy.
+// The device's access to the memory at p as the driver reports it (CU_POINTER_ATTRIBUTE_ACCESS_FLAGS:
+// 0 none, 1 read only, 3 read and write), or -1 when it cannot be asked. The driver call is looked
+// up through the runtime, so the library does not link the driver library itself.
+int device_access(const void *p) {
+  using Fn = CUresult (*)(void *, CUpointer_attribute, CUdeviceptr);
+  static const Fn fn = [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      (void)cudaGetLastError();
+      return static_cast<Fn>(nullptr);
+    }
+    return reinterpret_cast<Fn>(f);
+  }();
+  if (!fn) return -1;
+  unsigned long long v = 0;  // the driver writes a 4-byte enumerator into the low half
+  if (fn(&v, CU_POINTER_ATTRIBUTE_ACCESS_FLAGS, reinterpret_cast<CUdeviceptr>(p)) != CUDA_SUCCESS) return -1;
+  return (int)(v & 0xffffffffull);
+}
+
+// write: the kernels will store into the array, so memory registered read-only
+// (cudaHostRegisterReadOnly) is staged instead; reads need read access.
 template <class T>
-T *mapped_view(T *p, size_t bytes) {
+T *mapped_view(T *p, size_t bytes, bool write) {
   if (!p || bytes == 0) return nullptr;
   const char *lo = reinterpret_cast<const char *>(p), *hi = lo + bytes - 1;
   cudaPointerAttributes a{}, b{};
@@ -186,6 +211,9 @@ T *mapped_view(T *p, size_t bytes) {
   // both ends map into one contiguous device range (one allocation, no gap)
   if (static_cast<const char *>(b.devicePointer) - static_cast<const char *>(a.devicePointer) != (ptrdiff_t)(bytes - 1))
     return nullptr;
+  const int need = write ? CU_POINTER_ATTRIBUTE_ACCESS_FLAG_READWRITE : CU_POINTER_ATTRIBUTE_ACCESS_FLAG_READ;
+  const int acc = device_access(a.devicePointer);
+  if (acc < 0 || (acc & need) != need) return nullptr;
   return static_cast<T *>(a.devicePointer);
 }
 
@@ -402,7 +430,8 @@ int lbm_init_fields(lbm_ctx *c, const double *phi, const double *u, const double
   const long long N = c->N;
   const size_t bN = sizeof(double) * N;
   // page-locked inputs are read in place; the others are staged
-  const double *d_phi = mapped_view(phi, bN), *d_u = mapped_view(u, 3 * bN), *d_ps = mapped_view(pstar, bN);
+  const double *d_phi = mapped_view(phi, bN, false), *d_u = mapped_view(u, 3 * bN, false),
+               *d_ps = mapped_view(pstar, bN, false);
   int rc = LBM_OK;
   if ((!d_phi || !d_u || (pstar && !d_ps)) && (rc = ensure_stage(c, 5 * bN))) return rc;
   if (!d_phi) {
@@ -513,7 +542,8 @@ int lbm_read_fields(lbm_ctx *c, double *phi, double *u, double *pstar) {
   const long long N = c->N;
   const size_t bN = sizeof(double) * N;
   // page-locked outputs are written in place; the others are staged
-  double *o_phi = mapped_view(phi, bN), *o_u = mapped_view(u, 3 * bN), *o_ps = mapped_view(pstar, bN);
+  double *o_phi = mapped_view(phi, bN, true), *o_u = mapped_view(u, 3 * bN, true),
+         *o_ps = mapped_view(pstar, bN, true);
   int rc = LBM_OK;
   if (((phi && !o_phi) || (u && !o_u) || (pstar && !o_ps)) && (rc = ensure_stage(c, 5 * bN))) return rc;
   if (u || pstar) {

@@ -91,3 +91,4 @@ def test_pinned_view_inside_a_larger_allocation():
     assert np.array_equal(s[N:2 * N], ph) and np.array_equal(s[2 * N:5 * N], uu.reshape(-1))
     assert np.array_equal(s[5 * N:6 * N], pp)
     assert np.all(s[:N] == -7.0) and np.all(s[6 * N:] == -7.0)
+
